@@ -1,0 +1,213 @@
+/*
+ * kv.h -- batched log K_v(x), d/dv log K_v(x) and d/dx log K_v(x) on one GPU.
+ *
+ * The method is the fixed-bin integration of Takekawa, "Fast parallel calculation of modified
+ * Bessel function of the second kind and its derivatives" (arXiv 2108.11560):
+ *   K_v(x) = int_0^inf f(t) dt,  f(t) = cosh(vt) exp(-x cosh t)                 (Sec. 2, Eq. 1-2)
+ * Each pair brackets the peak t_p of g = log f (Sec. 2.2, Algorithms 1-2), finds the range
+ * [t0, t1] where f >= eps f(t_p) (Sec. 2.3), and sums a fixed number of trapezoid bins relative
+ * to the peak (Sec. 2.4, Eq. int; Algorithm 3).  The derivatives integrate t sinh(vt) e^{-x cosh t}
+ * and -cosh(t) cosh(vt) e^{-x cosh t} over the same bins (Sec. 4.1), each divided by the K sum.
+ *
+ * Conventions for every entry point below
+ *   - Arrays are structure-of-arrays, n contiguous elements each, caller-owned DEVICE memory
+ *     (except kv_fwd_bwd_host, which takes host memory).  The library never keeps a pointer
+ *     after the call's work on `stream` has finished.
+ *   - Element type is set by `dtype`: KV_F64 -> double for inputs and outputs;
+ *     KV_MIXED -> float for inputs and outputs.  Pointers must be aligned to the element size.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls are
+ *     asynchronous on that stream; argument errors are detected on the host before any launch.
+ *   - n == 0 is a valid no-op.  Output pointers may alias nothing else.
+ *   - Return value: KV_OK (0) or a negative kv_status; kv_strerror() describes it.
+ *
+ * Per-pair domain results (no error code; Sec. 2 defines K for v real, x > 0):
+ *   v < 0: uses |v| (K_{-v} = K_v) and negates d/dv.   v = 0: d/dv is exactly 0.
+ *   x = 0: log K = +inf, d/dv = +-inf (0 if v = 0), d/dx = -inf.
+ *   x = +inf: log K = -inf, d/dv = +-0, d/dx = -1.    |v| = inf, finite x > 0: +inf, +-inf, -inf.
+ *   x < 0 or NaN in v or x: NaN in every output.
+ */
+#ifndef KV_H_
+#define KV_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Arithmetic of the path (the `dtype` argument). */
+enum kv_dtype {
+    /* Everything in FP64: the paper's bracket (Algorithms 1-3) and the bins.  I/O double.
+     * Default eps: 2^-52 (machine epsilon, Sec. 2.1).  Default bins: 128. */
+    KV_F64 = 0,
+    /* Peak and log-offset g(t_p) in extended precision, bins in FP32 relative to the peak,
+     * with compensated sums.  I/O float.  Default eps: e^-20.  Default bins: 40 (32 suffice for
+     * x >= 1e-3; the corner of small v and x < 1e-4 needs 40 for 2e-6 in d/dx). */
+    KV_MIXED = 1
+};
+
+/* How the range [t0, t1] is found (kv_args.bracket). */
+enum kv_bracket_mode {
+    /* Algorithms 1-3 in FP64 (Sec. 2.2-2.3). */
+    KV_BRACKET_PLAIN = 0,
+    /* A 2-64-64-2 MLP on (v, log x) predicts (t0, t1); each pair checks g at both ends and falls
+     * back to KV_BRACKET_PLAIN when the check fails.  KV_MIXED only.  Needs kv_args.mlp. */
+    KV_BRACKET_MLP = 1
+};
+
+/* Status codes. */
+enum kv_status {
+    KV_OK = 0,
+    KV_ERR_NULL = -1,    /* a required pointer is NULL */
+    KV_ERR_SIZE = -2,    /* n < 0, or a size limit exceeded */
+    KV_ERR_BINS = -3,    /* bins < 1 or bins > KV_MAX_BINS */
+    KV_ERR_DTYPE = -4,   /* unknown dtype, or a mode not available for this dtype */
+    KV_ERR_ALIGN = -5,   /* a pointer is not aligned to its element size */
+    KV_ERR_CUDA = -6,    /* a CUDA runtime call or launch failed (see kv_last_cuda_error) */
+    KV_ERR_ARG = -7,     /* another argument is out of range (log_eps >= 0, max_iter < 1, ...) */
+    KV_ERR_HANDLE = -8,  /* a NULL or invalid MLP handle */
+    KV_ERR_IO = -9,      /* a checkpoint file could not be opened, read or written */
+    KV_ERR_FORMAT = -10, /* a checkpoint file has the wrong magic, version or sizes */
+    KV_ERR_NOMEM = -11   /* a device or host allocation failed */
+};
+
+#define KV_MAX_BINS 4096
+/* FindZero iterations (Algorithm 2: max_iter = 10). */
+#define KV_DEFAULT_MAX_ITER 10
+
+/* ------------------------------------------------------------------ the four core calls */
+
+/* log K_v(x) for n pairs (Algorithm 3 with Eq. int).  bins = the fixed n of Sec. 2.4. */
+int kv_log(const void* v, const void* x, void* logk, int64_t n, int bins, int dtype, void* stream);
+
+/* d/dv log K_v(x) (Sec. 4.1: integral of t sinh(vt) e^{-x cosh t} divided by K). */
+int kv_log_dv(const void* v, const void* x, void* dlogk_dv, int64_t n, int bins, int dtype,
+              void* stream);
+
+/* d/dx log K_v(x) (Sec. 4.1: integral of -cosh(t) cosh(vt) e^{-x cosh t} divided by K). */
+int kv_log_dx(const void* v, const void* x, void* dlogk_dx, int64_t n, int bins, int dtype,
+              void* stream);
+
+/* All three from one pass over the bins (one bracket per pair, reused by both derivatives). */
+int kv_fwd_bwd(const void* v, const void* x, void* logk, void* dv, void* dx, int64_t n, int bins,
+               int dtype, void* stream);
+
+/* ------------------------------------------------------------------ the extended call */
+
+typedef struct kv_mlp kv_mlp; /* opaque learned-bracket network, see below */
+
+typedef struct kv_args {
+    const void* v;        /* [n] orders */
+    const void* x;        /* [n] arguments */
+    void* logk;           /* [n] out, or NULL */
+    void* dv;             /* [n] out, or NULL */
+    void* dx;             /* [n] out, or NULL (at least one of logk, dv, dx is non-NULL) */
+    const void* grad_out; /* [n] or NULL: if set, dv and dx are multiplied by it (fused backward) */
+    int64_t n;
+    int bins;             /* 0 = the dtype's default */
+    int dtype;            /* enum kv_dtype */
+    int bracket;          /* enum kv_bracket_mode */
+    double log_eps;       /* log of the range's eps (< 0); 0 = the dtype's default */
+    int max_iter;         /* FindZero iterations; 0 = KV_DEFAULT_MAX_ITER */
+    int lanes;            /* lanes that share one pair's bins (1, 2, 4, 8, 16, 32); 0 = automatic */
+    const kv_mlp* mlp;    /* network for KV_BRACKET_MLP, else ignored */
+    uint8_t* status;      /* [n] or NULL: per-pair kv_pair_status bits */
+    unsigned long long* fallback_count; /* device counter or NULL: += pairs that fell back */
+    void* stream;
+} kv_args;
+
+/* Per-pair status bits written to kv_args.status. */
+enum kv_pair_status {
+    KV_PAIR_OK = 0,
+    KV_PAIR_EDGE = 1,        /* the pair is a domain edge case (see the list at the top) */
+    KV_PAIR_FALLBACK = 2,    /* the learned bracket failed its check; the plain one was used */
+    KV_PAIR_RANGE_CAP = 4    /* FindRange hit its doubling cap (input far outside any use) */
+};
+
+/* The general form of kv_fwd_bwd: bracket mode, eps, iteration count, lanes per pair,
+ * optional fused gradient epilogue, per-pair status and fallback counter. */
+int kv_fwd_bwd_ex(const kv_args* a);
+
+/* kv_fwd_bwd_ex on HOST buffers: a->v, a->x, a->logk, a->dv and a->dx are host pointers
+ * (pinned with cudaHostAlloc for full speed); every other field means what it means for
+ * kv_fwd_bwd_ex, except that grad_out, status and fallback_count must be NULL.  The call copies
+ * the inputs to the device, computes and copies the outputs back, pipelined in chunks of up to
+ * 2^22 pairs over a->stream and an internal second stream, and returns when the host outputs
+ * are complete.  Device staging memory is allocated and freed on the stream inside the call. */
+int kv_fwd_bwd_host(const kv_args* a);
+
+/* ------------------------------------------------------------------ building blocks */
+
+/* The plain bracket alone (Algorithms 1-3 through Sec. 2.3): per pair t0, t_p, t1 and the
+ * offset g(t_p), all double, for any dtype of v and x.  Outputs may be NULL individually. */
+int kv_bracket(const void* v, const void* x, double* t0, double* tp, double* t1, double* g_tp,
+               int64_t n, int dtype, double log_eps, int max_iter, void* stream);
+
+/* The backward epilogue on its own: grad_v = grad_out * dv, grad_x = grad_out * dx. */
+int kv_grad(const void* grad_out, const void* dv, const void* dx, void* grad_v, void* grad_x,
+            int64_t n, int dtype, void* stream);
+
+/* Deterministic sum of n elements (dtype's element type) into *out (one double, device memory).
+ * Used for the log-likelihood sum_i log K(v_i, x_i).  Scratch memory for the per-block partial
+ * sums is allocated and freed on `stream` (stream-ordered allocation). */
+int kv_sum(const void* a, int64_t n, int dtype, double* out, void* stream);
+
+/* ------------------------------------------------------------------ the learned bracket */
+/* A 2-64-64-2 MLP on (v, log x) -> (t0, t1) with ReLU hidden units; FP32 master weights for
+ * training, BF16 copies for inference with FP32 accumulation.  A handle owns its device memory. */
+
+/* New network with seeded random weights on the current device. */
+int kv_mlp_create(uint64_t seed, kv_mlp** out);
+/* Releases the handle and its device memory (NULL is a no-op). */
+int kv_mlp_free(kv_mlp* h);
+/* Checkpoint file: little-endian header (magic "KVMLP1\0\0", version, layer sizes, input and
+ * output scaling, Adam step) followed by FP32 weights and Adam moments. */
+int kv_mlp_save(const kv_mlp* h, const char* path);
+int kv_mlp_load(const char* path, kv_mlp** out);
+/* Host copies of the FP32 parameters in the order W1[64][2], b1[64], W2[64][64], b2[64],
+ * W3[2][64], b3[2] (4418 floats), and back. */
+int kv_mlp_get_params(const kv_mlp* h, float* host_params, int64_t count);
+int kv_mlp_set_params(kv_mlp* h, const float* host_params, int64_t count);
+#define KV_MLP_NPARAMS 4418
+
+typedef struct kv_train_args {
+    const double* v;      /* [n] device: training orders */
+    const double* x;      /* [n] device: training arguments */
+    const double* t0;     /* [n] device: target lower ends (from kv_bracket) */
+    const double* t1;     /* [n] device: target upper ends */
+    int64_t n;
+    int batch;            /* samples per Adam step */
+    int steps;            /* Adam steps to run */
+    float lr, beta1, beta2, adam_eps;
+    uint64_t seed;        /* sample order */
+    float* loss_out;      /* [steps] device or NULL: mean loss of each step's batch */
+    void* stream;
+} kv_train_args;
+
+/* Runs Adam steps on the mean squared error of the network's outputs against the scaled
+ * targets; forward, backward and the update are this library's kernels. */
+int kv_mlp_train(kv_mlp* h, const kv_train_args* a);
+
+/* Forward pass and gradient of one batch, without updating (for checks against a reference):
+ * loss (device double) and grads (device float[KV_MLP_NPARAMS]). */
+int kv_mlp_loss_grad(const kv_mlp* h, const double* v, const double* x, const double* t0,
+                     const double* t1, int64_t n, double* loss, float* grads, void* stream);
+
+/* Raw predictions (t0, t1) of the network, before any check. */
+int kv_mlp_predict(const kv_mlp* h, const void* v, const void* x, void* t0, void* t1, int64_t n,
+                   int dtype, void* stream);
+
+/* ------------------------------------------------------------------ diagnostics */
+/* Number of kernels this library has launched in this process (all threads, all devices). */
+uint64_t kv_launch_count(void);
+
+/* ------------------------------------------------------------------ errors */
+const char* kv_strerror(int code);
+/* The last CUDA error string seen by this thread's calls ("" if none). */
+const char* kv_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KV_H_ */

@@ -1,0 +1,197 @@
+// The fixed-bin trapezoid sums of Sec. 2.4 (Eq. int) and Sec. 4.1, for one pair, split over
+// L lanes of a warp (lane l takes bins l, l + L, ...).
+//
+// Every bin m in 0..n has t_m = t0 + m h and weight c_m exp(g(t_m) - g(t_p)), c_0 = c_n = 1/2.
+// Three sums share the weights:  S0 = sum w,  S1 = sum w t tanh(vt),  S2 = sum w cosh t.
+// Then log K = g(t_p) + log h + log S0,  d/dv log K = S1 / S0,  d/dx log K = -S2 / S0.
+//
+// The difference g(t_m) - g(t_p) is never formed by subtracting two large values.  With
+// s = t - t_p and u = v t_p (t, t_p >= 0):
+//   log cosh(vt) - log cosh(u) = v s + log1p(e^{-2vt}) - log1p(e^{-2u})
+//   x (cosh t - cosh t_p)      = 2 x sinh((t + t_p)/2) sinh(s/2)                    (FP64 bins)
+//                              = x sinh(t_p) s + (x e^{t_p}/2) phi(s) + (x e^{-t_p}/2) phi(-s)
+//                                with phi(s) = e^s - 1 - s >= 0                      (FP32 bins)
+// so that in FP32 every term is small where the weight is large and no two large terms cancel:
+//   g(t) - g(t_p) = (v - x sinh t_p) s + [log1p(e^{-2vt}) - log1p(e^{-2u})]
+//                   - (x e^{t_p}/2) phi(s) - (x e^{-t_p}/2) phi(-s).
+// The per-pair constants (v - x sinh t_p, x e^{+-t_p}/2, log1p(e^{-2u}), g(t_p)) are FP64.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace kvd {
+
+constexpr float LOG2E_F = 1.4426950408889634f;
+constexpr float LN2_F = 0.6931471805599453f;
+
+__device__ __forceinline__ float ex2_approx(float a)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float lg2_approx(float a)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float a)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
+// Compensated (Kahan) accumulation.
+template <typename T>
+struct KahanSum {
+    T s, c;
+    __device__ __forceinline__ void init() { s = T(0); c = T(0); }
+    __device__ __forceinline__ void add(T w)
+    {
+        T y = w - c;
+        T t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ T value() const { return s - c; }
+};
+
+template <typename T, int L>
+__device__ __forceinline__ T lane_sum(T a)
+{
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o, L);
+    return a;
+}
+
+// ------------------------------------------------------------------ FP64 bins
+
+struct BinsD {
+    double v, x, t0, h, tp, s0, Lu;  // s0 = t0 - t_p, Lu = log1p(e^{-2 v t_p})
+    int n;
+};
+
+template <int L, bool DERIV>
+__device__ __forceinline__ void sums_f64(const BinsD& b, int lane, double& S0, double& S1, double& S2)
+{
+    KahanSum<double> k0, k1, k2;
+    k0.init();
+    k1.init();
+    k2.init();
+    for (int m = lane; m <= b.n; m += L) {
+        double t = b.t0 + m * b.h;
+        double s = b.s0 + m * b.h;
+        double e2 = exp(-2.0 * b.v * t);
+        double dlc = b.v * s + (log1p(e2) - b.Lu);                   // log cosh(vt) - log cosh(u)
+        double dxc = 2.0 * b.x * sinh(0.5 * (t + b.tp)) * sinh(0.5 * s); // x (cosh t - cosh t_p)
+        double c = (m == 0 || m == b.n) ? 0.5 : 1.0;
+        double w = c * exp(dlc - dxc);
+        k0.add(w);
+        if (DERIV) {
+            k1.add(w * t * ((1.0 - e2) / (1.0 + e2)));
+            k2.add(w * cosh(t));
+        }
+    }
+    S0 = lane_sum<double, L>(k0.value());
+    S1 = DERIV ? lane_sum<double, L>(k1.value()) : 0.0;
+    S2 = DERIV ? lane_sum<double, L>(k2.value()) : 0.0;
+}
+
+// ------------------------------------------------------------------ FP32 bins
+
+struct BinsF {
+    float s0, h;    // s_m = s0 + m h
+    float v, u, tp; // |v|, v t_p, t_p
+    float c1;       // v - x sinh t_p
+    float ap, am;   // x e^{t_p} / 2, x e^{-t_p} / 2
+    float lu;       // log1p(e^{-2u})
+    float ep, em;   // e^{t_p}, e^{-t_p}
+    int n;
+};
+
+// phi(s) = e^s - 1 - s and phi(-s), and e^{+-s}, each to a few FP32 ulps relative.
+// |s| <= 2: even/odd Taylor parts of phi in z = s^2 (terms to s^15; the rest < 2e-9 relative).
+// |s| > 2: from expf (no cancellation there: phi(2) = 4.39, phi(-2) = 1.14).
+__device__ __forceinline__ void phi_pair(float s, float& php, float& phm, float& es, float& ems)
+{
+    if (fabsf(s) <= 2.0f) {
+        float z = s * s;
+        // E(z) = sum_{k>=1} z^{k-1}/(2k)!,  O(z) = sum_{k>=1} z^{k-1}/(2k+1)!
+        float E = 1.0f / 87178291200.0f;  // 1/14!
+        E = fmaf(E, z, 1.0f / 479001600.0f);
+        E = fmaf(E, z, 1.0f / 3628800.0f);
+        E = fmaf(E, z, 1.0f / 40320.0f);
+        E = fmaf(E, z, 1.0f / 720.0f);
+        E = fmaf(E, z, 1.0f / 24.0f);
+        E = fmaf(E, z, 0.5f);
+        float O = 1.0f / 1307674368000.0f;  // 1/15!
+        O = fmaf(O, z, 1.0f / 6227020800.0f);
+        O = fmaf(O, z, 1.0f / 39916800.0f);
+        O = fmaf(O, z, 1.0f / 362880.0f);
+        O = fmaf(O, z, 1.0f / 5040.0f);
+        O = fmaf(O, z, 1.0f / 120.0f);
+        O = fmaf(O, z, 1.0f / 6.0f);
+        float so = s * O;
+        php = z * (E + so);
+        phm = z * (E - so);
+        es = (1.0f + s) + php;
+        ems = (1.0f - s) + phm;
+    } else {
+        es = expf(s);
+        ems = expf(-s);
+        php = (es - 1.0f) - s;
+        phm = (ems - 1.0f) + s;
+    }
+}
+
+// tanh(y) for |y| < 0.625 by its Taylor series through y^19 (relative error < 1e-8 there);
+// (1 - e^{-2y}) / (1 + e^{-2y}) loses relative precision to the cancellation in 1 - e^{-2y}.
+__device__ __forceinline__ float tanh_small(float y)
+{
+    float z = y * y;
+    float p = -443861162.0f / 1856156927625.0f;
+    p = fmaf(p, z, 6404582.0f / 10854718875.0f);
+    p = fmaf(p, z, -929569.0f / 638512875.0f);
+    p = fmaf(p, z, 21844.0f / 6081075.0f);
+    p = fmaf(p, z, -1382.0f / 155925.0f);
+    p = fmaf(p, z, 62.0f / 2835.0f);
+    p = fmaf(p, z, -17.0f / 315.0f);
+    p = fmaf(p, z, 2.0f / 15.0f);
+    p = fmaf(p, z, -1.0f / 3.0f);
+    return fmaf(y * z, p, y);
+}
+
+template <int L, bool DERIV>
+__device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, float& S1, float& S2)
+{
+    KahanSum<float> k0, k1, k2;
+    k0.init();
+    k1.init();
+    k2.init();
+    for (int m = lane; m <= b.n; m += L) {
+        float s = fmaf((float)m, b.h, b.s0);
+        float php, phm, es, ems;
+        phi_pair(s, php, phm, es, ems);
+        float vt = fmaf(b.v, s, b.u);
+        float e2 = ex2_approx(-2.0f * LOG2E_F * vt);             // e^{-2vt}
+        float d = fmaf(lg2_approx(1.0f + e2), LN2_F, -b.lu);      // log1p(e^{-2vt}) - log1p(e^{-2u})
+        float dg = fmaf(b.c1, s, d) - fmaf(b.ap, php, b.am * phm);
+        float c = (m == 0 || m == b.n) ? 0.5f : 1.0f;
+        float w = c * ex2_approx(dg * LOG2E_F);
+        k0.add(w);
+        if (DERIV) {
+            float t = b.tp + s;
+            float th = fabsf(vt) < 0.625f ? tanh_small(vt)
+                                          : (1.0f - e2) * rcp_approx(1.0f + e2);  // tanh(vt)
+            k1.add(w * (t * th));
+            k2.add(w * (0.5f * fmaf(b.ep, es, b.em * ems)));     // cosh t
+        }
+    }
+    S0 = lane_sum<float, L>(k0.value());
+    S1 = DERIV ? lane_sum<float, L>(k1.value()) : 0.0f;
+    S2 = DERIV ? lane_sum<float, L>(k2.value()) : 0.0f;
+}
+
+}  // namespace kvd

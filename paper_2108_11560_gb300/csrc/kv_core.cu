@@ -1,0 +1,644 @@
+// Core kernels and C-ABI entry points of the batched log K_v(x) library (see include/kv.h).
+//
+// One (v, x) pair is handled by a group of L lanes of one warp (L = 1 for large batches): every
+// lane runs the pair's bracket (Algorithms 1-3, FP64) and then its share of the bins (Sec. 2.4,
+// Sec. 4.1); the partial sums meet by warp shuffles.  Warps iterate over pair groups in a
+// grid-stride loop so that all lanes of a warp make the same number of trips (the shuffles need
+// the whole warp); pairs past the end are computed on dummy inputs and not stored.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "kv_bins.cuh"
+#include "kv_bracket.cuh"
+#include "kv_internal.h"
+
+#include <atomic>
+
+namespace {
+thread_local char g_last_cuda_error[256] = "";
+std::atomic<uint64_t> g_launches{0};
+}
+
+namespace kvh {
+
+int cuda_fail(cudaError_t e)
+{
+    snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s", cudaGetErrorName(e),
+             cudaGetErrorString(e));
+    return KV_ERR_CUDA;
+}
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int sm_count()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (cache[dev] == 0) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = n > 0 ? n : 1;
+    }
+    return cache[dev];
+}
+
+}  // namespace kvh
+
+namespace {
+
+using namespace kvd;
+
+constexpr int kBlock = 128;
+
+struct KParams {
+    const void* v;
+    const void* x;
+    void* logk;
+    void* dv;
+    void* dx;
+    const void* go;
+    uint8_t* status;
+    int64_t n;
+    int bins;
+    double log_eps;
+    int max_iter;
+};
+
+// Domain edge cases (the list at the top of kv.h).  Returns true and fills the outputs for an
+// edge pair; false for a regular pair (finite v, finite x > 0).
+__device__ __forceinline__ bool edge_pair(double v, double x, double& lk, double& dv, double& dx)
+{
+    if (isnan(v) || isnan(x) || x < 0.0) {
+        lk = dv = dx = nan("");
+        return true;
+    }
+    if (x == 0.0) {
+        lk = INFINITY;
+        dv = (v == 0.0) ? 0.0 : copysign(INFINITY, v);
+        dx = -INFINITY;
+        return true;
+    }
+    if (isinf(x)) {
+        lk = -INFINITY;
+        dv = copysign(0.0, v);
+        dx = -1.0;
+        return true;
+    }
+    if (isinf(v)) {
+        lk = INFINITY;
+        dv = copysign(INFINITY, v);
+        dx = -INFINITY;
+        return true;
+    }
+    return false;
+}
+
+__device__ __noinline__ BracketD bracket_call(double v, double x, double log_eps, int max_iter)
+{
+    return bracket_f64(v, x, log_eps, max_iter);
+}
+
+template <typename T>
+__device__ __forceinline__ void store_outputs(const KParams& p, int64_t i, double lk, double dv,
+                                              double dx, uint8_t st)
+{
+    if (p.go) {
+        double g = (double)((const T*)p.go)[i];
+        dv *= g;
+        dx *= g;
+    }
+    if (p.logk) ((T*)p.logk)[i] = (T)lk;
+    if (p.dv) ((T*)p.dv)[i] = (T)dv;
+    if (p.dx) ((T*)p.dx)[i] = (T)dx;
+    if (p.status) p.status[i] = st;
+}
+
+// FP64 plain path: the paper's bracket and bins, all in double.
+template <int L, bool DERIV>
+__global__ void __launch_bounds__(kBlock) kv_f64_kernel(KParams p)
+{
+    const int lane = threadIdx.x % L;
+    constexpr int G = 32 / L;  // pair groups per warp
+    const int g = (threadIdx.x % 32) / L;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
+    for (int64_t base = warp * G; base < p.n; base += nwarps * G) {
+        const int64_t i = base + g;
+        const bool active = i < p.n;
+        double v = active ? ((const double*)p.v)[i] : 1.0;
+        double x = active ? ((const double*)p.x)[i] : 1.0;
+        double lk, dv, dx;
+        const bool edge = edge_pair(v, x, lk, dv, dx);
+        const double va = edge ? 1.0 : fabs(v);
+        const double xa = edge ? 1.0 : x;
+        BracketD br = bracket_call(va, xa, p.log_eps, p.max_iter);
+        BinsD b;
+        b.v = va;
+        b.x = xa;
+        b.t0 = br.t0;
+        b.h = (br.t1 - br.t0) / p.bins;
+        b.tp = br.tp;
+        b.s0 = br.t0 - br.tp;
+        b.Lu = log1p(exp(-2.0 * va * br.tp));
+        b.n = p.bins;
+        double S0, S1, S2;
+        sums_f64<L, DERIV>(b, lane, S0, S1, S2);
+        if (active && lane == 0) {
+            uint8_t st = KV_PAIR_OK;
+            if (edge) {
+                st = KV_PAIR_EDGE;
+            } else {
+                lk = br.G + log(b.h) + log(S0);
+                dv = DERIV ? copysign(S1 / S0, v) : 0.0;
+                if (v == 0.0) dv = 0.0;
+                dx = DERIV ? -(S2 / S0) : 0.0;
+                if (br.capped) st = KV_PAIR_RANGE_CAP;
+            }
+            store_outputs<double>(p, i, lk, dv, dx, st);
+        }
+    }
+}
+
+// Mixed path with the plain FP64 bracket: FP64 peak, offset and per-pair constants, FP32 bins.
+template <int L, bool DERIV>
+__global__ void __launch_bounds__(kBlock) kv_mixed_kernel(KParams p)
+{
+    const int lane = threadIdx.x % L;
+    constexpr int G = 32 / L;
+    const int g = (threadIdx.x % 32) / L;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
+    for (int64_t base = warp * G; base < p.n; base += nwarps * G) {
+        const int64_t i = base + g;
+        const bool active = i < p.n;
+        double v = active ? (double)((const float*)p.v)[i] : 1.0;
+        double x = active ? (double)((const float*)p.x)[i] : 1.0;
+        double lk, dv, dx;
+        const bool edge = edge_pair(v, x, lk, dv, dx);
+        const double va = edge ? 1.0 : fabs(v);
+        const double xa = edge ? 1.0 : x;
+        BracketD br = bracket_call(va, xa, p.log_eps, p.max_iter);
+        const double ep = exp(br.tp), em = 1.0 / ep;
+        const double u = va * br.tp;
+        const double h = (br.t1 - br.t0) / p.bins;
+        BinsF b;
+        b.s0 = (float)(br.t0 - br.tp);
+        b.h = (float)h;
+        b.v = (float)va;
+        b.u = (float)u;
+        b.tp = (float)br.tp;
+        b.c1 = (float)(va - xa * 0.5 * (ep - em));
+        b.ap = (float)(xa * 0.5 * ep);
+        b.am = (float)(xa * 0.5 * em);
+        b.lu = (float)log1p(exp(-2.0 * u));
+        b.ep = (float)ep;
+        b.em = (float)em;
+        b.n = p.bins;
+        float S0, S1, S2;
+        sums_f32<L, DERIV>(b, lane, S0, S1, S2);
+        if (active && lane == 0) {
+            uint8_t st = KV_PAIR_OK;
+            if (edge) {
+                st = KV_PAIR_EDGE;
+            } else {
+                lk = br.G + (double)logf(b.h * S0);
+                float r = 1.0f / S0;
+                dv = DERIV ? copysign((double)(S1 * r), v) : 0.0;
+                if (v == 0.0) dv = 0.0;
+                dx = DERIV ? -(double)(S2 * r) : 0.0;
+                if (br.capped) st = KV_PAIR_RANGE_CAP;
+            }
+            store_outputs<float>(p, i, lk, dv, dx, st);
+        }
+    }
+}
+
+// The bracket alone, for training targets and checks.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) kv_bracket_kernel(const T* v, const T* x, double* t0,
+                                                            double* tp, double* t1, double* gtp,
+                                                            int64_t n, double log_eps, int max_iter)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double vv = fabs((double)v[i]), xx = (double)x[i];
+        double lk, dv, dx;
+        if (edge_pair((double)v[i], xx, lk, dv, dx)) {
+            if (t0) t0[i] = nan("");
+            if (tp) tp[i] = nan("");
+            if (t1) t1[i] = nan("");
+            if (gtp) gtp[i] = nan("");
+            continue;
+        }
+        BracketD br = bracket_call(vv, xx, log_eps, max_iter);
+        if (t0) t0[i] = br.t0;
+        if (tp) tp[i] = br.tp;
+        if (t1) t1[i] = br.t1;
+        if (gtp) gtp[i] = br.G;
+    }
+}
+
+template <typename T>
+__global__ void kv_grad_kernel(const T* go, const T* dv, const T* dx, T* gv, T* gx, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        T g = go[i];
+        if (gv) gv[i] = g * dv[i];
+        if (gx) gx[i] = g * dx[i];
+    }
+}
+
+// Deterministic two-stage sum: fixed grid for a given n, fixed reduction order.
+constexpr int kSumBlock = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kSumBlock) kv_sum_partial(const T* a, int64_t n, double* part)
+{
+    __shared__ double sh[kSumBlock];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kSumBlock + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kSumBlock)
+        acc += (double)a[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = kSumBlock / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(kSumBlock) kv_sum_final(const double* part, int nb, double* out)
+{
+    __shared__ double sh[kSumBlock];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += kSumBlock) acc += part[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = kSumBlock / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+// ------------------------------------------------------------------ host side
+
+template <typename K>
+int resident_blocks(K kernel)
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kBlock, 0) != cudaSuccess || b < 1)
+        b = 1;
+    return b;
+}
+
+template <typename K>
+int launch_pairs(K kernel, const KParams& p, int lanes, cudaStream_t s)
+{
+    // persistent grid: at most the resident blocks of every SM, at least enough for the pairs
+    int64_t threads = ((p.n * lanes + 31) / 32) * 32;
+    int64_t need = (threads + kBlock - 1) / kBlock;
+    int64_t cap = (int64_t)kvh::sm_count() * resident_blocks(kernel);
+    int grid = (int)(need < cap ? need : cap);
+    if (grid < 1) grid = 1;
+    kernel<<<grid, kBlock, 0, s>>>(p);
+    KV_LAUNCH_CHECK();
+    return KV_OK;
+}
+
+template <int L>
+int dispatch_deriv(const KParams& p, int dtype, bool deriv, cudaStream_t s)
+{
+    if (dtype == KV_F64)
+        return deriv ? launch_pairs(kv_f64_kernel<L, true>, p, L, s)
+                     : launch_pairs(kv_f64_kernel<L, false>, p, L, s);
+    return deriv ? launch_pairs(kv_mixed_kernel<L, true>, p, L, s)
+                 : launch_pairs(kv_mixed_kernel<L, false>, p, L, s);
+}
+
+int auto_lanes(int64_t n)
+{
+    // enough threads to fill every SM with about 1024 resident threads
+    int64_t want = (int64_t)kvh::sm_count() * 1024;
+    int L = 1;
+    while (L < 32 && n * L < want) L *= 2;
+    return L;
+}
+
+int validate(const kv_args* a, int* bins, double* log_eps, int* max_iter, int* lanes)
+{
+    if (!a) return KV_ERR_NULL;
+    if (a->dtype != KV_F64 && a->dtype != KV_MIXED) return KV_ERR_DTYPE;
+    if (a->n < 0) return KV_ERR_SIZE;
+    if (a->n > 0 && (!a->v || !a->x)) return KV_ERR_NULL;
+    if (a->n > 0 && !a->logk && !a->dv && !a->dx) return KV_ERR_NULL;
+    *bins = a->bins == 0 ? (a->dtype == KV_F64 ? 128 : 40) : a->bins;
+    if (*bins < 1 || *bins > KV_MAX_BINS) return KV_ERR_BINS;
+    *log_eps = a->log_eps == 0.0 ? (a->dtype == KV_F64 ? -52.0 * kvd::LN2_D : -20.0) : a->log_eps;
+    if (!(*log_eps < 0.0) || !isfinite(*log_eps)) return KV_ERR_ARG;
+    *max_iter = a->max_iter == 0 ? KV_DEFAULT_MAX_ITER : a->max_iter;
+    if (*max_iter < 1 || *max_iter > 64) return KV_ERR_ARG;
+    int L = a->lanes == 0 ? auto_lanes(a->n) : a->lanes;
+    if (L != 1 && L != 2 && L != 4 && L != 8 && L != 16 && L != 32) return KV_ERR_ARG;
+    *lanes = L;
+    if (a->bracket != KV_BRACKET_PLAIN && a->bracket != KV_BRACKET_MLP) return KV_ERR_ARG;
+    if (a->bracket == KV_BRACKET_MLP) {
+        if (a->dtype != KV_MIXED) return KV_ERR_DTYPE;
+        if (!a->mlp) return KV_ERR_HANDLE;
+    }
+    size_t es = kvh::elem_size(a->dtype);
+    const void* ptrs[6] = {a->v, a->x, a->logk, a->dv, a->dx, a->grad_out};
+    for (const void* q : ptrs)
+        if (q && !kvh::aligned(q, es)) return KV_ERR_ALIGN;
+    return KV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kv_fwd_bwd_ex(const kv_args* a)
+{
+    int bins, max_iter, lanes;
+    double log_eps;
+    int rc = validate(a, &bins, &log_eps, &max_iter, &lanes);
+    if (rc != KV_OK) return rc;
+    if (a->n == 0) return KV_OK;
+    if (a->bracket == KV_BRACKET_MLP) return kvh::launch_mlp_path(a, bins, log_eps, max_iter);
+    KParams p;
+    p.v = a->v;
+    p.x = a->x;
+    p.logk = a->logk;
+    p.dv = a->dv;
+    p.dx = a->dx;
+    p.go = a->grad_out;
+    p.status = a->status;
+    p.n = a->n;
+    p.bins = bins;
+    p.log_eps = log_eps;
+    p.max_iter = max_iter;
+    const bool deriv = a->dv || a->dx;
+    cudaStream_t s = (cudaStream_t)a->stream;
+    switch (lanes) {
+        case 1: return dispatch_deriv<1>(p, a->dtype, deriv, s);
+        case 2: return dispatch_deriv<2>(p, a->dtype, deriv, s);
+        case 4: return dispatch_deriv<4>(p, a->dtype, deriv, s);
+        case 8: return dispatch_deriv<8>(p, a->dtype, deriv, s);
+        case 16: return dispatch_deriv<16>(p, a->dtype, deriv, s);
+        default: return dispatch_deriv<32>(p, a->dtype, deriv, s);
+    }
+}
+
+static int core_call(const void* v, const void* x, void* logk, void* dv, void* dx, int64_t n,
+                     int bins, int dtype, void* stream)
+{
+    if (bins == 0) return KV_ERR_BINS;  // the four core calls take an explicit bin count
+    kv_args a;
+    memset(&a, 0, sizeof(a));
+    a.v = v;
+    a.x = x;
+    a.logk = logk;
+    a.dv = dv;
+    a.dx = dx;
+    a.n = n;
+    a.bins = bins;
+    a.dtype = dtype;
+    a.stream = stream;
+    return kv_fwd_bwd_ex(&a);
+}
+
+int kv_log(const void* v, const void* x, void* logk, int64_t n, int bins, int dtype, void* stream)
+{
+    if (n > 0 && !logk) return KV_ERR_NULL;
+    return core_call(v, x, logk, nullptr, nullptr, n, bins, dtype, stream);
+}
+
+int kv_log_dv(const void* v, const void* x, void* dlogk_dv, int64_t n, int bins, int dtype,
+              void* stream)
+{
+    if (n > 0 && !dlogk_dv) return KV_ERR_NULL;
+    return core_call(v, x, nullptr, dlogk_dv, nullptr, n, bins, dtype, stream);
+}
+
+int kv_log_dx(const void* v, const void* x, void* dlogk_dx, int64_t n, int bins, int dtype,
+              void* stream)
+{
+    if (n > 0 && !dlogk_dx) return KV_ERR_NULL;
+    return core_call(v, x, nullptr, nullptr, dlogk_dx, n, bins, dtype, stream);
+}
+
+int kv_fwd_bwd(const void* v, const void* x, void* logk, void* dv, void* dx, int64_t n, int bins,
+               int dtype, void* stream)
+{
+    if (n > 0 && (!logk || !dv || !dx)) return KV_ERR_NULL;
+    return core_call(v, x, logk, dv, dx, n, bins, dtype, stream);
+}
+
+int kv_bracket(const void* v, const void* x, double* t0, double* tp, double* t1, double* g_tp,
+               int64_t n, int dtype, double log_eps, int max_iter, void* stream)
+{
+    if (dtype != KV_F64 && dtype != KV_MIXED) return KV_ERR_DTYPE;
+    if (n < 0) return KV_ERR_SIZE;
+    if (n == 0) return KV_OK;
+    if (!v || !x) return KV_ERR_NULL;
+    if (!t0 && !tp && !t1 && !g_tp) return KV_ERR_NULL;
+    if (log_eps == 0.0) log_eps = dtype == KV_F64 ? -52.0 * kvd::LN2_D : -20.0;
+    if (!(log_eps < 0.0) || !isfinite(log_eps)) return KV_ERR_ARG;
+    if (max_iter == 0) max_iter = KV_DEFAULT_MAX_ITER;
+    if (max_iter < 1 || max_iter > 64) return KV_ERR_ARG;
+    size_t es = kvh::elem_size(dtype);
+    if (!kvh::aligned(v, es) || !kvh::aligned(x, es)) return KV_ERR_ALIGN;
+    const void* outs[4] = {t0, tp, t1, g_tp};
+    for (const void* q : outs)
+        if (q && !kvh::aligned(q, 8)) return KV_ERR_ALIGN;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t need = (n + kBlock - 1) / kBlock;
+    int64_t cap = (int64_t)kvh::sm_count() * 8;
+    int grid = (int)(need < cap ? need : cap);
+    if (dtype == KV_F64)
+        kv_bracket_kernel<double><<<grid, kBlock, 0, s>>>((const double*)v, (const double*)x, t0, tp,
+                                                          t1, g_tp, n, log_eps, max_iter);
+    else
+        kv_bracket_kernel<float><<<grid, kBlock, 0, s>>>((const float*)v, (const float*)x, t0, tp,
+                                                         t1, g_tp, n, log_eps, max_iter);
+    KV_LAUNCH_CHECK();
+    return KV_OK;
+}
+
+int kv_grad(const void* grad_out, const void* dv, const void* dx, void* grad_v, void* grad_x,
+            int64_t n, int dtype, void* stream)
+{
+    if (dtype != KV_F64 && dtype != KV_MIXED) return KV_ERR_DTYPE;
+    if (n < 0) return KV_ERR_SIZE;
+    if (n == 0) return KV_OK;
+    if (!grad_out || (!grad_v && !grad_x)) return KV_ERR_NULL;
+    if ((grad_v && !dv) || (grad_x && !dx)) return KV_ERR_NULL;
+    size_t es = kvh::elem_size(dtype);
+    const void* ptrs[5] = {grad_out, dv, dx, grad_v, grad_x};
+    for (const void* q : ptrs)
+        if (q && !kvh::aligned(q, es)) return KV_ERR_ALIGN;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t need = (n + 255) / 256;
+    int64_t cap = (int64_t)kvh::sm_count() * 16;
+    int grid = (int)(need < cap ? need : cap);
+    if (dtype == KV_F64)
+        kv_grad_kernel<double><<<grid, 256, 0, s>>>((const double*)grad_out, (const double*)dv,
+                                                    (const double*)dx, (double*)grad_v,
+                                                    (double*)grad_x, n);
+    else
+        kv_grad_kernel<float><<<grid, 256, 0, s>>>((const float*)grad_out, (const float*)dv,
+                                                   (const float*)dx, (float*)grad_v, (float*)grad_x,
+                                                   n);
+    KV_LAUNCH_CHECK();
+    return KV_OK;
+}
+
+// Number of partial sums for n elements: a function of n only, so results are reproducible.
+static int sum_blocks(int64_t n)
+{
+    int64_t b = (n + 4095) / 4096;
+    if (b < 1) b = 1;
+    if (b > 1024) b = 1024;
+    return (int)b;
+}
+
+int kv_sum(const void* a, int64_t n, int dtype, double* out, void* stream)
+{
+    if (dtype != KV_F64 && dtype != KV_MIXED) return KV_ERR_DTYPE;
+    if (n < 0) return KV_ERR_SIZE;
+    if (!out || (n > 0 && !a)) return KV_ERR_NULL;
+    if (!kvh::aligned(out, 8) || (a && !kvh::aligned(a, kvh::elem_size(dtype)))) return KV_ERR_ALIGN;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        KV_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double), s));
+        return KV_OK;
+    }
+    int nb = sum_blocks(n);
+    double* part = nullptr;
+    KV_CUDA_TRY(cudaMallocAsync((void**)&part, sizeof(double) * nb, s));
+    if (dtype == KV_F64)
+        kv_sum_partial<double><<<nb, kSumBlock, 0, s>>>((const double*)a, n, part);
+    else
+        kv_sum_partial<float><<<nb, kSumBlock, 0, s>>>((const float*)a, n, part);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        kvh::note_launch();
+        kv_sum_final<<<1, kSumBlock, 0, s>>>(part, nb, out);
+        kvh::note_launch();
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaFreeAsync(part, s);
+    if (e != cudaSuccess) return kvh::cuda_fail(e);
+    if (e2 != cudaSuccess) return kvh::cuda_fail(e2);
+    return KV_OK;
+}
+
+// Host-buffer form: chunks alternate between the caller's stream and an internal one; each
+// stream copies its chunk in, computes it and copies it out in order, so the copies of one
+// stream overlap the kernels of the other.
+int kv_fwd_bwd_host(const kv_args* h)
+{
+    if (!h) return KV_ERR_NULL;
+    if (h->grad_out || h->status || h->fallback_count) return KV_ERR_ARG;
+    int bins_, max_iter_, lanes_;
+    double log_eps_;
+    int rc = validate(h, &bins_, &log_eps_, &max_iter_, &lanes_);
+    if (rc != KV_OK) return rc;
+    const int64_t n = h->n;
+    if (n == 0) return KV_OK;
+    const size_t es = kvh::elem_size(h->dtype);
+    const int64_t chunk = n < (int64_t)(1 << 22) ? n : (int64_t)(1 << 22);
+    const int nslots = n > chunk ? 2 : 1;
+    cudaStream_t st[2];
+    st[0] = (cudaStream_t)h->stream;
+    st[1] = nullptr;
+    if (nslots == 2) KV_CUDA_TRY(cudaStreamCreateWithFlags(&st[1], cudaStreamNonBlocking));
+    char* buf[2] = {nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < nslots && e == cudaSuccess; ++k)
+        e = cudaMallocAsync((void**)&buf[k], 5 * es * chunk, st[0]);
+    cudaEvent_t ready = nullptr;
+    if (e == cudaSuccess && nslots == 2) {
+        e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ready, st[0]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st[1], ready, 0);
+    }
+    for (int64_t off = 0, c = 0; e == cudaSuccess && rc == KV_OK && off < n; off += chunk, ++c) {
+        const int k = (int)(c % nslots);
+        const int64_t m = (n - off) < chunk ? (n - off) : chunk;
+        char* dvin = buf[k];
+        char* dxin = dvin + es * chunk;
+        char* dl = dvin + 2 * es * chunk;
+        char* ddv = dvin + 3 * es * chunk;
+        char* ddx = dvin + 4 * es * chunk;
+        e = cudaMemcpyAsync(dvin, (const char*)h->v + es * off, es * m, cudaMemcpyHostToDevice, st[k]);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dxin, (const char*)h->x + es * off, es * m, cudaMemcpyHostToDevice,
+                                st[k]);
+        if (e != cudaSuccess) break;
+        kv_args d = *h;
+        d.v = dvin;
+        d.x = dxin;
+        d.logk = h->logk ? dl : nullptr;
+        d.dv = h->dv ? ddv : nullptr;
+        d.dx = h->dx ? ddx : nullptr;
+        d.n = m;
+        d.stream = st[k];
+        rc = kv_fwd_bwd_ex(&d);
+        if (rc != KV_OK) break;
+        if (h->logk)
+            e = cudaMemcpyAsync((char*)h->logk + es * off, dl, es * m, cudaMemcpyDeviceToHost, st[k]);
+        if (e == cudaSuccess && h->dv)
+            e = cudaMemcpyAsync((char*)h->dv + es * off, ddv, es * m, cudaMemcpyDeviceToHost, st[k]);
+        if (e == cudaSuccess && h->dx)
+            e = cudaMemcpyAsync((char*)h->dx + es * off, ddx, es * m, cudaMemcpyDeviceToHost, st[k]);
+    }
+    // join the second stream back before the buffers go
+    if (nslots == 2 && ready) {
+        cudaError_t e2 = cudaEventRecord(ready, st[1]);
+        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(st[0], ready, 0);
+        if (e == cudaSuccess) e = e2;
+    }
+    for (int k = 0; k < nslots; ++k)
+        if (buf[k]) {
+            cudaError_t e2 = cudaFreeAsync(buf[k], st[0]);
+            if (e == cudaSuccess) e = e2;
+        }
+    cudaError_t e3 = cudaStreamSynchronize(st[0]);
+    if (e == cudaSuccess) e = e3;
+    if (ready) cudaEventDestroy(ready);
+    if (st[1]) cudaStreamDestroy(st[1]);
+    if (rc != KV_OK) return rc;
+    if (e != cudaSuccess) return kvh::cuda_fail(e);
+    return KV_OK;
+}
+
+const char* kv_strerror(int code)
+{
+    switch (code) {
+        case KV_OK: return "ok";
+        case KV_ERR_NULL: return "a required pointer is NULL";
+        case KV_ERR_SIZE: return "n < 0 or a size limit exceeded";
+        case KV_ERR_BINS: return "bins out of range [1, KV_MAX_BINS]";
+        case KV_ERR_DTYPE: return "unknown dtype or mode not available for this dtype";
+        case KV_ERR_ALIGN: return "a pointer is not aligned to its element size";
+        case KV_ERR_CUDA: return "a CUDA call failed (see kv_last_cuda_error)";
+        case KV_ERR_ARG: return "an argument is out of range";
+        case KV_ERR_HANDLE: return "NULL or invalid MLP handle";
+        case KV_ERR_IO: return "checkpoint file could not be opened, read or written";
+        case KV_ERR_FORMAT: return "checkpoint file has the wrong magic, version or sizes";
+        case KV_ERR_NOMEM: return "allocation failed";
+        default: return "unknown status";
+    }
+}
+
+const char* kv_last_cuda_error(void) { return g_last_cuda_error; }
+
+uint64_t kv_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,52 @@
+// Shared host-side helpers of the library's translation units (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/kv.h"
+
+namespace kvh {
+
+// Records a CUDA error string for kv_last_cuda_error() and returns KV_ERR_CUDA.
+int cuda_fail(cudaError_t e);
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+inline size_t elem_size(int dtype) { return dtype == KV_F64 ? 8 : 4; }
+
+#define KV_CUDA_TRY(expr)                          \
+    do {                                           \
+        cudaError_t kv_e_ = (expr);                \
+        if (kv_e_ != cudaSuccess) return kvh::cuda_fail(kv_e_); \
+    } while (0)
+
+// Counts one kernel launch (kv_launch_count) and checks it.
+void note_launch();
+#define KV_LAUNCH_CHECK()     \
+    do {                      \
+        kvh::note_launch();   \
+        KV_CUDA_TRY(cudaGetLastError()); \
+    } while (0)
+
+// The learned-bracket network as the kernels see it (device pointers owned by the handle).
+struct MlpView {
+    const float* w1;            // [64][2]  FP32
+    const float* b1;            // [64]
+    const unsigned short* w2h;  // [64][64] BF16 bits (row = output unit)
+    const float* b2;            // [64]
+    const float* w3;            // [2][64]
+    const float* b3;            // [2]
+    float in_scale[4];          // a = v * in_scale[0] + in_scale[1], b = log x * in_scale[2] + in_scale[3]
+    float out_scale[4];         // t0 = y0 * out_scale[0] + out_scale[1], width = softplus(y1) * out_scale[2]
+};
+
+// Fills a view of the handle's inference weights; returns KV_OK or KV_ERR_HANDLE.
+int mlp_view(const kv_mlp* h, MlpView* out);
+
+// Launches the learned-bracket kernel (kv_mlp.cu).  Arguments are already validated.
+int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter);
+
+}  // namespace kvh
