@@ -153,6 +153,25 @@ int kv_grad(const void* grad_out, const void* dv, const void* dx, void* grad_v, 
  * sums is allocated and freed on `stream` (stream-ordered allocation). */
 int kv_sum(const void* a, int64_t n, int dtype, double* out, void* stream);
 
+/* The same deterministic sum for callers that cannot allocate device memory: applications whose
+ * device memory is all reserved up front (a framework's caching allocator, or a fixed memory
+ * budget), so that an allocation inside a library call would fail or would take memory the
+ * caller has promised elsewhere.  The paper has no counterpart; this is a property of the
+ * library, not of the method.
+ *   - The partial sums live in a device array inside this library, sized for at most
+ *     KV_SUM_NOALLOC_MAX_N elements (128 KiB, held on every GPU that loads the library until the
+ *     process exits).  n > KV_SUM_NOALLOC_MAX_N returns KV_ERR_SIZE before any GPU work.
+ *   - The call allocates and frees nothing.  Its first call on a device looks up the array's
+ *     device address (cudaGetSymbolAddress), once per device; make that first call before any
+ *     stream capture.
+ *   - All calls on a device share the array: calls whose work can overlap on the GPU (streams
+ *     with no ordering between them) race on it, so the caller must order them.  Each call
+ *     overwrites the partial sums it uses, so nothing needs clearing between calls.
+ * Arguments, result and errors are otherwise those of kv_sum; for n up to 4,194,304 the
+ * reduction order, and so the result, is the same as kv_sum's. */
+#define KV_SUM_NOALLOC_MAX_N 67108864
+int kv_sum_noalloc(const void* a, int64_t n, int dtype, double* out, void* stream);
+
 /* ------------------------------------------------------------------ the learned bracket */
 /* A 2-64-64-2 MLP on (v, log x) -> (t0, t1) with ReLU hidden units; FP32 master weights for
  * training, BF16 copies for inference with FP32 accumulation.  A handle owns its device memory. */

@@ -21,12 +21,13 @@ KV_BRACKET_MLP = 1
 KV_OK = 0
 KV_MAX_BINS = 4096
 KV_MLP_NPARAMS = 4418
+KV_SUM_NOALLOC_MAX_N = 67108864
 KV_PAIR_OK, KV_PAIR_EDGE, KV_PAIR_FALLBACK, KV_PAIR_RANGE_CAP = 0, 1, 2, 4
 
 #: every function include/kv.h declares
 EXPORTED = [
     "kv_log", "kv_log_dv", "kv_log_dx", "kv_fwd_bwd", "kv_fwd_bwd_ex", "kv_fwd_bwd_host",
-    "kv_bracket", "kv_grad", "kv_sum", "kv_mlp_create", "kv_mlp_free", "kv_mlp_save",
+    "kv_bracket", "kv_grad", "kv_sum", "kv_sum_noalloc", "kv_mlp_create", "kv_mlp_free", "kv_mlp_save",
     "kv_mlp_load", "kv_mlp_get_params", "kv_mlp_set_params", "kv_mlp_train",
     "kv_mlp_loss_grad", "kv_mlp_predict", "kv_launch_count", "kv_strerror",
     "kv_last_cuda_error",
@@ -66,6 +67,7 @@ def _declare(lib):
         "kv_bracket": [P, P, P, P, P, P, I64, I, D, I, P],
         "kv_grad": [P, P, P, P, P, I64, I, P],
         "kv_sum": [P, I64, I, P, P],
+        "kv_sum_noalloc": [P, I64, I, P, P],
         "kv_mlp_create": [ctypes.c_uint64, ctypes.POINTER(P)],
         "kv_mlp_free": [P],
         "kv_mlp_save": [P, ctypes.c_char_p],
