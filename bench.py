@@ -193,7 +193,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--bins", type=int, default=32)
-    ap.add_argument("--bracket", choices=("mlp", "plain"), default="plain")
+    ap.add_argument("--bracket", choices=("mlp", "plain"), default="mlp")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")

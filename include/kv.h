@@ -185,10 +185,10 @@ int kv_mlp_free(kv_mlp* h);
 int kv_mlp_save(const kv_mlp* h, const char* path);
 int kv_mlp_load(const char* path, kv_mlp** out);
 /* Host copies of the FP32 parameters in the order W1[64][2], b1[64], W2[64][64], b2[64],
- * W3[2][64], b3[2] (4418 floats), and back. */
+ * W3[2][64], b3[2] (4482 floats), and back. */
 int kv_mlp_get_params(const kv_mlp* h, float* host_params, int64_t count);
 int kv_mlp_set_params(kv_mlp* h, const float* host_params, int64_t count);
-#define KV_MLP_NPARAMS 4418
+#define KV_MLP_NPARAMS 4482
 
 typedef struct kv_train_args {
     const double* v;      /* [n] device: training orders */

@@ -8,7 +8,7 @@ Algorithms 1-3 finds).  Layout and arithmetic, written out plainly:
   layer 2    h2 = relu(W2 h1 + b2)                         W2: 64 x 64
   layer 3    y  = W3 h2 + b3                               W3: 2 x 64
   outputs    L_k = y_k * OUT_SCALE[2k] + OUT_SCALE[2k+1]   (k = 0, 1)
-             t0 = max(t_ref - (e^{L_0} - DELTA), 0),  t1 = t_ref + max(e^{L_1} - DELTA, 0)
+             t0 = max(t_ref - max(e^{L_0} - DELTA, 0), 0),  t1 = t_ref + max(e^{L_1} - DELTA, 0)
   targets    L_0* = ln(t_p - t0* + DELTA),  L_1* = ln(t1* - t_p + DELTA)   from a plain bracket
   loss       mean over the batch of ((y_0 - T_0)^2 + (y_1 - T_1)^2) / 2,
              T_k = (L_k* - OUT_SCALE[2k+1]) / OUT_SCALE[2k]
@@ -17,7 +17,7 @@ Algorithms 1-3 finds).  Layout and arithmetic, written out plainly:
   batches    sample k of step j is index  mix(seed + j * batch + k) mod n  with mix the SplitMix64
              finalizer (Steele, Lea & Flood 2014) of its argument plus 0x9e3779b97f4a7c15.
 
-Parameter vector order: W1[64][2], b1[64], W2[64][64], b2[64], W3[2][64], b3[2] (4418 values).
+Parameter vector order: W1[64][2], b1[64], W2[64][64], b2[64], W3[2][64], b3[2] (4482 values).
 """
 from __future__ import annotations
 
@@ -69,10 +69,26 @@ def forward(p, v, x):
     return {"f": f, "z1": z1, "h1": h1, "z2": z2, "h2": h2, "y": y}
 
 
+def peak(v, x, iters: int = 60):
+    """The peak t_p of g (Sec. 2.1-2.2): 0 if v^2 <= x, else the zero of
+    g'(t) = v tanh(vt) - x sinh t.  Newton's method from asinh(v/x), where g' <= 0 (tanh <= 1);
+    g' is concave (g''' <= 0), so the iterates decrease monotonically to the zero."""
+    v = np.abs(np.asarray(v, dtype=np.float64))
+    x = np.asarray(x, dtype=np.float64)
+    t = np.arcsinh(v / x)
+    for _ in range(iters):
+        th = np.tanh(v * t)
+        g1 = v * th - x * np.sinh(t)
+        g2 = v * v * (1 - th * th) - x * np.cosh(t)
+        step = np.where(g2 != 0, g1 / np.where(g2 != 0, g2, 1.0), 0.0)
+        t = np.clip(t - step, 0.0, t)
+    return np.where(v * v > x, t, 0.0)
+
+
 def targets(t0, tp, t1):
-    """Normalised targets (T_0, T_1) from a plain bracket."""
-    L0 = np.log(np.asarray(tp) - np.asarray(t0) + DELTA)
-    L1 = np.log(np.asarray(t1) - np.asarray(tp) + DELTA)
+    """Normalised targets (T_0, T_1) from a range [t0, t1] around the peak tp."""
+    L0 = np.log(np.maximum(np.asarray(tp) - np.asarray(t0), 0.0) + DELTA)
+    L1 = np.log(np.maximum(np.asarray(t1) - np.asarray(tp), 0.0) + DELTA)
     return np.stack([(L0 - OUT_SCALE[1]) / OUT_SCALE[0], (L1 - OUT_SCALE[3]) / OUT_SCALE[2]], axis=1)
 
 
@@ -110,7 +126,7 @@ def predict(p, v, x, t_ref):
     L0 = y[:, 0] * OUT_SCALE[0] + OUT_SCALE[1]
     L1 = y[:, 1] * OUT_SCALE[2] + OUT_SCALE[3]
     t_ref = np.asarray(t_ref, dtype=np.float64)
-    t0 = np.maximum(t_ref - (np.exp(L0) - DELTA), 0.0)
+    t0 = np.maximum(t_ref - np.maximum(np.exp(L0) - DELTA, 0.0), 0.0)
     t1 = t_ref + np.maximum(np.exp(L1) - DELTA, 0.0)
     return t0, t1
 
@@ -129,13 +145,15 @@ def batch_indices(seed: int, step: int, batch: int, n: int):
                     dtype=np.int64)
 
 
-def train(p, v, x, t0, tp, t1, steps, batch, lr, beta1, beta2, eps, seed):
-    """Plain Adam training loop; returns (params, per-step losses)."""
+def train(p, v, x, t0, t1, steps, batch, lr, beta1, beta2, eps, seed, step0=0):
+    """Plain Adam training loop on brackets (t0, t1) around the peak of each pair; returns
+    (params, per-step losses).  step0 continues the step count of an earlier call."""
     p = np.array(p, dtype=np.float64)
+    tp = peak(v, x)
     m = np.zeros_like(p)
     s = np.zeros_like(p)
     losses = []
-    for j in range(steps):
+    for j in range(step0, step0 + steps):
         idx = batch_indices(seed, j, batch, len(v))
         loss, g = loss_grad(p, v[idx], x[idx], t0[idx], tp[idx], t1[idx])
         losses.append(loss)

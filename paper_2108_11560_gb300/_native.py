@@ -20,7 +20,7 @@ KV_BRACKET_PLAIN = 0
 KV_BRACKET_MLP = 1
 KV_OK = 0
 KV_MAX_BINS = 4096
-KV_MLP_NPARAMS = 4418
+KV_MLP_NPARAMS = 4482
 KV_SUM_NOALLOC_MAX_N = 67108864
 KV_PAIR_OK, KV_PAIR_EDGE, KV_PAIR_FALLBACK, KV_PAIR_RANGE_CAP = 0, 1, 2, 4
 

@@ -163,6 +163,27 @@ __device__ __forceinline__ float tanh_small(float y)
     return fmaf(y * z, p, y);
 }
 
+// g(t_p + s) - g(t_p) in FP32 by the cancellation-free form above (the FP32 bin formula), with
+// e^{-2vt} and e^{+-s} returned for the derivative integrands.
+__device__ __forceinline__ float delta_g_f32(const BinsF& b, float s, float& e2, float& es,
+                                             float& ems)
+{
+    float php, phm;
+    phi_pair(s, php, phm, es, ems);
+    float vt = fmaf(b.v, s, b.u);
+    e2 = ex2_approx(-2.0f * LOG2E_F * vt);
+    float d = fmaf(lg2_approx(1.0f + e2), LN2_F, -b.lu);
+    return fmaf(b.c1, s, d) - fmaf(b.ap, php, b.am * phm);
+}
+
+// d/ds of delta_g_f32 at the same s, from the values it returned: g'(t_p + s) written as
+// (v - x sinh t_p) - 2v e^{-2vt} / (1 + e^{-2vt}) - (x e^{t_p}/2)(e^s - 1) + (x e^{-t_p}/2)(e^{-s} - 1).
+__device__ __forceinline__ float delta_g_slope_f32(const BinsF& b, float e2, float es, float ems)
+{
+    float dl = -2.0f * b.v * e2 * rcp_approx(1.0f + e2);
+    return b.c1 + dl - b.ap * (es - 1.0f) + b.am * (ems - 1.0f);
+}
+
 template <int L, bool DERIV>
 __device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, float& S1, float& S2)
 {

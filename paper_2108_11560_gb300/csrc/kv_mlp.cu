@@ -1,46 +1,947 @@
-// The learned bracket (2-64-64-2 MLP) -- handle management, inference and training kernels.
+// The learned bracket: a 2-64-64-2 MLP on (v, log x) that predicts the range [t0, t1] of
+// Sec. 2.3, replacing Algorithms 1-3 on the hot path, with a per-pair check of g at the ends and
+// a fallback to the plain FP64 bracket.
+//
+// Network (all parameters FP32 masters; inference reads W2 as BF16 with FP32 accumulation):
+//   a = v * in[0] + in[1],  b = ln x * in[2] + in[3]
+//   h1 = relu(W1 [a b] + b1),  h2 = relu(W2 h1 + b2),  y = W3 h2 + b3
+//   L_k = y_k * out[2k] + out[2k+1];  t0 = max(t_ref - (e^{L_0} - DELTA), 0),
+//   t1 = t_ref + max(e^{L_1} - DELTA, 0), with t_ref the peak of g.
+// The network predicts log half-widths of the range about the peak; the peak itself comes from
+// four FP32 Newton steps on g' from asinh(v/x) (g' is concave and <= 0 there, so the iterates
+// fall monotonically onto the zero).
+//
+// Fast path per pair (kv_mlp_kernel): MLP -> peak -> float-float offset g(t_ref) and constants
+// -> check that g - g(t_ref) at both ends lies in [log eps - W, log eps] (the range is neither
+// too narrow nor too wide) -> FP32 bins.  Pairs that fail the check are appended to a list and
+// recomputed by a second kernel with the plain FP64 bracket, so one failing lane does not stall
+// its warp on the slow path.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
 
+#include <vector>
+
+#include "kv_bins.cuh"
+#include "kv_bracket.cuh"
+#include "kv_dfloat.cuh"
 #include "kv_internal.h"
 
+namespace {
+
+constexpr int H = 64;
+constexpr int NP = KV_MLP_NPARAMS;  // 4482
+// offsets of W1[64][2], b1[64], W2[64][64], b2[64], W3[2][64], b3[2] in the parameter vector
+constexpr int OFF_W1 = 0, OFF_B1 = 2 * H, OFF_W2 = OFF_B1 + H, OFF_B2 = OFF_W2 + H * H,
+              OFF_W3 = OFF_B2 + H, OFF_B3 = OFF_W3 + 2 * H;
+static_assert(OFF_B3 + 2 == NP, "parameter layout");
+constexpr float DELTA = 1e-3f;
+constexpr uint32_t kMagic = 0x4b564d4cu;  // handle tag
+constexpr double kWindow = 12.0;          // nats of allowed over-width at each end
+
+}  // namespace
+
 struct kv_mlp {
-    int magic;
+    uint32_t magic;
+    int device;
+    float* params;           // [NP] FP32 masters
+    float* adam_m;           // [NP]
+    float* adam_s;           // [NP]
+    unsigned short* w2h;     // [H*H] BF16 copy of W2
+    int64_t step;            // Adam steps taken
+    float in_scale[4];
+    float out_scale[4];
 };
+
+namespace {
+
+using namespace kvd;
+
+bool valid(const kv_mlp* h) { return h && h->magic == kMagic && h->params; }
+
+uint64_t mix64(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t mix64_d(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+unsigned short bf16_bits_host(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return (unsigned short)((u >> 16) | 0x40);  // NaN
+    u += 0x7fffu + ((u >> 16) & 1u);  // round to nearest even
+    return (unsigned short)(u >> 16);
+}
+
+int upload(kv_mlp* h, const float* host)
+{
+    KV_CUDA_TRY(cudaMemcpy(h->params, host, sizeof(float) * NP, cudaMemcpyHostToDevice));
+    std::vector<unsigned short> w2(H * H);
+    for (int k = 0; k < H * H; ++k) w2[k] = bf16_bits_host(host[OFF_W2 + k]);
+    KV_CUDA_TRY(cudaMemcpy(h->w2h, w2.data(), sizeof(unsigned short) * H * H, cudaMemcpyHostToDevice));
+    return KV_OK;
+}
+
+int alloc_handle(kv_mlp** out)
+{
+    kv_mlp* h = new kv_mlp;
+    memset(h, 0, sizeof(*h));
+    h->magic = kMagic;
+    cudaGetDevice(&h->device);
+    cudaError_t e = cudaMalloc((void**)&h->params, sizeof(float) * NP);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->adam_m, sizeof(float) * NP);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->adam_s, sizeof(float) * NP);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->w2h, sizeof(unsigned short) * H * H);
+    if (e == cudaSuccess) e = cudaMemset(h->adam_m, 0, sizeof(float) * NP);
+    if (e == cudaSuccess) e = cudaMemset(h->adam_s, 0, sizeof(float) * NP);
+    if (e != cudaSuccess) {
+        cudaFree(h->params);
+        cudaFree(h->adam_m);
+        cudaFree(h->adam_s);
+        cudaFree(h->w2h);
+        delete h;
+        return kvh::cuda_fail(e);
+    }
+    // feature and output scaling: v in [0, 200] and log10 x in [-4, 4] map to [-1, 1]
+    h->in_scale[0] = 1.0f / 100.0f;
+    h->in_scale[1] = -1.0f;
+    h->in_scale[2] = (float)(1.0 / (4.0 * log(10.0)));
+    h->in_scale[3] = 0.0f;
+    h->out_scale[0] = 3.0f;
+    h->out_scale[1] = -3.0f;
+    h->out_scale[2] = 2.0f;
+    h->out_scale[3] = -1.0f;
+    *out = h;
+    return KV_OK;
+}
+
+// ------------------------------------------------------------------ device pieces
+
+// The peak of g by four FP32 Newton steps from asinh(v/x) (0 when v^2 <= x).
+__device__ __forceinline__ float peak_f32(float v, float x)
+{
+    if (!(v * v > x)) return 0.0f;
+    float t = asinhf(v / x);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float e2 = ex2_approx(-2.0f * LOG2E_F * v * t);
+        float r = rcp_approx(1.0f + e2);
+        float th = (1.0f - e2) * r;
+        float sech2 = 4.0f * e2 * r * r;
+        float et = expf(t);
+        float eti = 1.0f / et;
+        float g1 = v * th - 0.5f * x * (et - eti);
+        float g2 = v * v * sech2 - 0.5f * x * (et + eti);
+        float tn = t - g1 / g2;
+        if (isfinite(tn)) t = fminf(fmaxf(tn, 0.0f), t);
+    }
+    return t;
+}
+
+struct MlpSmem {
+    float w1[2 * H], b1[H], w2[H * H], b2[H], w3[2 * H], b3[2];
+    float in_scale[4], out_scale[4];
+};
+
+// Forward pass of one pair on the CUDA cores: log half-widths (L0, L1).  W2 holds the BF16
+// weights widened to FP32; h1 is rounded to BF16 as the tensor-core form would see it.
+__device__ __forceinline__ void mlp_forward(const MlpSmem& s, float v, float x, float& L0, float& L1)
+{
+    const float a = fmaf(v, s.in_scale[0], s.in_scale[1]);
+    const float b = fmaf(__logf(x), s.in_scale[2], s.in_scale[3]);
+    float h1[H];
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        float z = fmaf(s.w1[2 * i], a, fmaf(s.w1[2 * i + 1], b, s.b1[i]));
+        h1[i] = __bfloat162float(__float2bfloat16_rn(fmaxf(z, 0.0f)));
+    }
+    float y0 = s.b3[0], y1 = s.b3[1];
+    for (int j = 0; j < H; ++j) {
+        const float4* row = reinterpret_cast<const float4*>(&s.w2[j * H]);
+        float acc = s.b2[j];
+#pragma unroll
+        for (int q = 0; q < H / 4; ++q) {
+            float4 w = row[q];
+            acc = fmaf(w.x, h1[4 * q], acc);
+            acc = fmaf(w.y, h1[4 * q + 1], acc);
+            acc = fmaf(w.z, h1[4 * q + 2], acc);
+            acc = fmaf(w.w, h1[4 * q + 3], acc);
+        }
+        float h2 = fmaxf(acc, 0.0f);
+        y0 = fmaf(s.w3[j], h2, y0);
+        y1 = fmaf(s.w3[H + j], h2, y1);
+    }
+    L0 = fmaf(y0, s.out_scale[0], s.out_scale[1]);
+    L1 = fmaf(y1, s.out_scale[2], s.out_scale[3]);
+}
+
+__device__ void load_mlp_smem(MlpSmem& s, const kvh::MlpView& m)
+{
+    for (int k = threadIdx.x; k < 2 * H; k += blockDim.x) {
+        s.w1[k] = m.w1[k];
+        s.w3[k] = m.w3[k];
+    }
+    for (int k = threadIdx.x; k < H; k += blockDim.x) {
+        s.b1[k] = m.b1[k];
+        s.b2[k] = m.b2[k];
+    }
+    for (int k = threadIdx.x; k < H * H; k += blockDim.x)
+        s.w2[k] = __uint_as_float(((uint32_t)m.w2h[k]) << 16);
+    if (threadIdx.x < 2) s.b3[threadIdx.x] = m.b3[threadIdx.x];
+    if (threadIdx.x < 4) {
+        s.in_scale[threadIdx.x] = m.in_scale[threadIdx.x];
+        s.out_scale[threadIdx.x] = m.out_scale[threadIdx.x];
+    }
+}
+
+// Per-pair constants of the FP32 bins at the reference point tr, with the offset g(tr) as a
+// float-float (no FP64): G = v tr + log1p(e^{-2 v tr}) - ln 2 - x cosh tr.
+struct PeakConst {
+    df G;
+    BinsF b;
+};
+
+__device__ __forceinline__ PeakConst peak_constants(float v, float x, float tr)
+{
+    PeakConst c;
+    df E = df_exp(tr);
+    df Ei = df_rcp(E);
+    df u = two_prod(v, tr);
+    float lu = log1pf(expf(-2.0f * u.hi));
+    df ch = df_mul_f(df_add(E, Ei), 0.5f * x);  // x cosh tr
+    df sh = df_mul_f(df_sub(E, Ei), 0.5f * x);  // x sinh tr
+    c.G = df_sub(df_add(df_add(u, df_make(lu)), df_neg(df_ln2())), ch);
+    df c1 = df_sub(df_make(v), sh);
+    c.b.v = v;
+    c.b.u = u.hi;
+    c.b.tp = tr;
+    c.b.c1 = c1.hi + c1.lo;
+    c.b.ap = 0.5f * x * E.hi;
+    c.b.am = 0.5f * x * Ei.hi;
+    c.b.lu = lu;
+    c.b.ep = E.hi;
+    c.b.em = Ei.hi;
+    return c;
+}
+
+struct MlpPathParams {
+    const float* v;
+    const float* x;
+    float* logk;
+    float* dv;
+    float* dx;
+    const float* go;
+    uint8_t* status;
+    int64_t n;
+    int bins;
+    float log_eps;
+    uint32_t* fb_list;
+    uint32_t* fb_count;
+    kvh::MlpView mlp;
+};
+
+constexpr int kMlpBlock = 128;
+
+__device__ __forceinline__ bool float_edge(float v, float x, float& lk, float& dv, float& dx)
+{
+    if (isnan(v) || isnan(x) || x < 0.0f) {
+        lk = dv = dx = nanf("");
+        return true;
+    }
+    if (x == 0.0f) {
+        lk = INFINITY;
+        dv = (v == 0.0f) ? 0.0f : copysignf(INFINITY, v);
+        dx = -INFINITY;
+        return true;
+    }
+    if (isinf(x)) {
+        lk = -INFINITY;
+        dv = copysignf(0.0f, v);
+        dx = -1.0f;
+        return true;
+    }
+    if (isinf(v)) {
+        lk = INFINITY;
+        dv = copysignf(INFINITY, v);
+        dx = -INFINITY;
+        return true;
+    }
+    return false;
+}
+
+template <bool DERIV>
+__global__ void __launch_bounds__(kMlpBlock) kv_mlp_kernel(MlpPathParams p)
+{
+    __shared__ MlpSmem sm;
+    load_mlp_smem(sm, p.mlp);
+    __syncthreads();
+    const float lo_ok = p.log_eps - (float)kWindow;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = p.v[i], x = p.x[i];
+        float lk, dv, dx;
+        if (float_edge(v, x, lk, dv, dx)) {
+            if (p.go) {
+                dv *= p.go[i];
+                dx *= p.go[i];
+            }
+            if (p.logk) p.logk[i] = lk;
+            if (p.dv) p.dv[i] = dv;
+            if (p.dx) p.dx[i] = dx;
+            if (p.status) p.status[i] = KV_PAIR_EDGE;
+            continue;
+        }
+        const float va = fabsf(v);
+        float L0, L1;
+        mlp_forward(sm, va, x, L0, L1);
+        const float tr = peak_f32(va, x);
+        const float w0 = fmaxf(__expf(L0) - DELTA, 0.0f);
+        const float w1 = fmaxf(__expf(L1) - DELTA, 1e-6f * (1.0f + tr));
+        PeakConst c = peak_constants(va, x, tr);
+        // The check: g - g(tr) at each end within [log eps - W, log eps].  An end that misses
+        // the window gets one FP32 Newton step towards the middle of the window (the slope of
+        // the same cancellation-free difference), then must pass the same check.
+        const float mid = p.log_eps - 0.5f * (float)kWindow;
+        auto in_window = [&](float d) { return d <= p.log_eps && d >= lo_ok; };
+        float e2, es, ems;
+        float s1 = w1;
+        float d1 = delta_g_f32(c.b, s1, e2, es, ems);
+        if (!in_window(d1)) {
+            const float slope = delta_g_slope_f32(c.b, e2, es, ems);
+            float sn = s1 - (d1 - mid) / slope;
+            if (!(slope < 0.0f) || !isfinite(sn)) sn = d1 > p.log_eps ? 2.0f * s1 : 0.5f * s1;
+            s1 = fminf(fmaxf(sn, 0.25f * s1), 4.0f * s1);
+            d1 = delta_g_f32(c.b, s1, e2, es, ems);
+        }
+        bool ok = in_window(d1);
+        const float t1 = tr + s1;
+        float t0 = 0.0f;
+        if (tr > 0.0f) {
+            // the left end: the predicted one, or 0 when the range reaches it
+            float s0 = -fminf(w0, tr);
+            float dz = delta_g_f32(c.b, -tr, e2, es, ems);  // at t = 0
+            if (dz > p.log_eps || (s0 <= -tr && dz >= lo_ok)) {
+                t0 = 0.0f;  // the range starts at 0 and is not too wide there
+            } else {
+                float d0 = s0 <= -tr ? dz : delta_g_f32(c.b, s0, e2, es, ems);
+                if (!in_window(d0)) {
+                    const float slope = delta_g_slope_f32(c.b, e2, es, ems);
+                    float sn = s0 - (d0 - mid) / slope;
+                    if (!(slope > 0.0f) || !isfinite(sn)) sn = d0 > p.log_eps ? 2.0f * s0 : 0.5f * s0;
+                    s0 = fmaxf(fminf(sn, 0.25f * s0), 4.0f * s0);
+                    if (s0 <= -tr) {
+                        s0 = -tr;
+                        d0 = dz;
+                    } else {
+                        d0 = delta_g_f32(c.b, s0, e2, es, ems);
+                    }
+                }
+                ok = ok && (in_window(d0) || (s0 <= -tr && d0 >= lo_ok));
+                t0 = fmaxf(tr + s0, 0.0f);
+            }
+        }
+        if (!ok) {
+            uint32_t k = atomicAdd(p.fb_count, 1u);
+            p.fb_list[k] = (uint32_t)i;
+            continue;
+        }
+        c.b.s0 = t0 - tr;
+        c.b.h = (t1 - t0) / (float)p.bins;
+        c.b.n = p.bins;
+        float S0, S1, S2;
+        sums_f32<1, DERIV>(c.b, 0, S0, S1, S2);
+        df L = df_add(c.G, df_make(logf(c.b.h * S0)));
+        lk = L.hi + L.lo;
+        const float r = 1.0f / S0;
+        dv = DERIV ? copysignf(S1 * r, v) : 0.0f;
+        if (v == 0.0f) dv = 0.0f;
+        dx = DERIV ? -(S2 * r) : 0.0f;
+        if (p.go) {
+            dv *= p.go[i];
+            dx *= p.go[i];
+        }
+        if (p.logk) p.logk[i] = lk;
+        if (p.dv) p.dv[i] = dv;
+        if (p.dx) p.dx[i] = dx;
+        if (p.status) p.status[i] = KV_PAIR_OK;
+    }
+}
+
+struct FallbackParams {
+    MlpPathParams p;
+    double log_eps;
+    int max_iter;
+    unsigned long long* fallback_total;
+};
+
+// The pairs whose learned bracket failed its check: the plain FP64 bracket (Algorithms 1-3) and
+// FP64 constants, then the same FP32 bins.
+template <bool DERIV>
+__global__ void __launch_bounds__(kMlpBlock) kv_fallback_kernel(FallbackParams f)
+{
+    const MlpPathParams& p = f.p;
+    const uint32_t cnt = *p.fb_count;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && f.fallback_total)
+        atomicAdd(f.fallback_total, (unsigned long long)cnt);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+        const int64_t i = p.fb_list[k];
+        const double v = (double)p.v[i], x = (double)p.x[i];
+        const double va = fabs(v);
+        BracketD br = bracket_f64(va, x, f.log_eps, f.max_iter);
+        const double ep = exp(br.tp), em = 1.0 / ep;
+        const double u = va * br.tp;
+        const double h = (br.t1 - br.t0) / p.bins;
+        BinsF b;
+        b.s0 = (float)(br.t0 - br.tp);
+        b.h = (float)h;
+        b.v = (float)va;
+        b.u = (float)u;
+        b.tp = (float)br.tp;
+        b.c1 = (float)(va - x * 0.5 * (ep - em));
+        b.ap = (float)(x * 0.5 * ep);
+        b.am = (float)(x * 0.5 * em);
+        b.lu = (float)log1p(exp(-2.0 * u));
+        b.ep = (float)ep;
+        b.em = (float)em;
+        b.n = p.bins;
+        float S0, S1, S2;
+        sums_f32<1, DERIV>(b, 0, S0, S1, S2);
+        double lk = br.G + (double)logf(b.h * S0);
+        float r = 1.0f / S0;
+        double dv = DERIV ? copysign((double)(S1 * r), v) : 0.0;
+        if (v == 0.0) dv = 0.0;
+        double dx = DERIV ? -(double)(S2 * r) : 0.0;
+        if (p.go) {
+            dv *= (double)p.go[i];
+            dx *= (double)p.go[i];
+        }
+        if (p.logk) p.logk[i] = (float)lk;
+        if (p.dv) p.dv[i] = (float)dv;
+        if (p.dx) p.dx[i] = (float)dx;
+        if (p.status) p.status[i] = KV_PAIR_FALLBACK | (br.capped ? KV_PAIR_RANGE_CAP : 0);
+    }
+}
+
+// ------------------------------------------------------------------ raw predictions
+
+__global__ void __launch_bounds__(kMlpBlock) kv_predict_kernel(kvh::MlpView m, const float* v,
+                                                               const float* x, float* t0,
+                                                               float* t1, int64_t n)
+{
+    __shared__ MlpSmem sm;
+    load_mlp_smem(sm, m);
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float va = fabsf(v[i]);
+        float L0, L1;
+        mlp_forward(sm, va, x[i], L0, L1);
+        const float tr = peak_f32(va, x[i]);
+        t0[i] = fmaxf(tr - fmaxf(__expf(L0) - DELTA, 0.0f), 0.0f);
+        t1[i] = tr + fmaxf(__expf(L1) - DELTA, 0.0f);
+    }
+}
+
+// ------------------------------------------------------------------ training
+
+constexpr int kTrainBlock = 128;  // samples per block
+
+struct GradArgs {
+    const float* params;
+    const double* v;
+    const double* x;
+    const double* t0;
+    const double* t1;
+    int64_t n;
+    int batch;
+    int64_t step;
+    uint64_t seed;
+    int sequential;  // 1: sample k of the batch is element k (no shuffling)
+    float* partial;  // [gridDim.x][NP + 1]
+    float in_scale[4];
+    float out_scale[4];
+};
+
+// Per-block forward and backward of 128 samples, then the block's share of the parameter
+// gradients (and of the loss) as sums over its samples, written to partial[block].
+__global__ void __launch_bounds__(kTrainBlock) mlp_grad_kernel(GradArgs g)
+{
+    // per-sample vectors are stored unit-major with a padded stride (X[i * kPad + sample]), so
+    // that both the per-sample loops and the per-parameter sums over samples are conflict-free
+    constexpr int kPad = kTrainBlock + 1;
+    extern __shared__ float sh[];
+    float* W = sh;                              // [NP]
+    float* F = W + NP + 2;                      // [128][2] features
+    float* DY = F + 2 * kTrainBlock;            // [128][2]
+    float* LS = DY + 2 * kTrainBlock;           // [128] per-sample loss
+    float* H1 = LS + kTrainBlock;               // [64][kPad]
+    float* H2 = H1 + H * kPad;                  // [64][kPad]
+    float* DZ2 = H2 + H * kPad;                 // [64][kPad]
+    float* DZ1 = DZ2 + H * kPad;                // [64][kPad]
+    for (int k = threadIdx.x; k < NP; k += blockDim.x) W[k] = g.params[k];
+    __syncthreads();
+    const int s = threadIdx.x;
+    const int64_t kb = (int64_t)blockIdx.x * kTrainBlock + s;
+    const bool active = kb < g.batch;
+    struct Col {
+        float* p;
+        __device__ float& operator[](int i) const { return p[i * kPad]; }
+    };
+    Col h1{H1 + s}, h2{H2 + s}, dz2{DZ2 + s}, dz1{DZ1 + s};
+    if (active) {
+        const int64_t idx = g.sequential ? kb : (int64_t)(mix64_d(g.seed + (uint64_t)g.step * g.batch + kb) % (uint64_t)g.n);
+        const double vd = fabs(g.v[idx]), xd = g.x[idx];
+        const float a = (float)(vd * g.in_scale[0] + g.in_scale[1]);
+        const float b = (float)(log(xd) * g.in_scale[2] + g.in_scale[3]);
+        F[2 * s] = a;
+        F[2 * s + 1] = b;
+        for (int i = 0; i < H; ++i)
+            h1[i] = fmaxf(fmaf(W[OFF_W1 + 2 * i], a, fmaf(W[OFF_W1 + 2 * i + 1], b, W[OFF_B1 + i])), 0.0f);
+        float y0 = W[OFF_B3], y1 = W[OFF_B3 + 1];
+        for (int j = 0; j < H; ++j) {
+            float acc = W[OFF_B2 + j];
+            for (int i = 0; i < H; ++i) acc = fmaf(W[OFF_W2 + j * H + i], h1[i], acc);
+            float z = fmaxf(acc, 0.0f);
+            h2[j] = z;
+            y0 = fmaf(W[OFF_W3 + j], z, y0);
+            y1 = fmaf(W[OFF_W3 + H + j], z, y1);
+        }
+        // targets: log half-widths about the peak
+        const float tr = peak_f32((float)vd, (float)xd);
+        const double T0 = (log(fmax((double)tr - g.t0[idx], 0.0) + (double)DELTA) - g.out_scale[1]) / g.out_scale[0];
+        const double T1 = (log(fmax(g.t1[idx] - (double)tr, 0.0) + (double)DELTA) - g.out_scale[3]) / g.out_scale[2];
+        const float r0 = y0 - (float)T0, r1 = y1 - (float)T1;
+        LS[s] = 0.5f * (r0 * r0 + r1 * r1);
+        const float dy0 = r0 / (float)g.batch, dy1 = r1 / (float)g.batch;
+        DY[2 * s] = dy0;
+        DY[2 * s + 1] = dy1;
+        for (int j = 0; j < H; ++j)
+            dz2[j] = h2[j] > 0.0f ? fmaf(W[OFF_W3 + j], dy0, W[OFF_W3 + H + j] * dy1) : 0.0f;
+        for (int i = 0; i < H; ++i) {
+            float acc = 0.0f;
+            for (int j = 0; j < H; ++j) acc = fmaf(W[OFF_W2 + j * H + i], dz2[j], acc);
+            dz1[i] = h1[i] > 0.0f ? acc : 0.0f;
+        }
+    } else {
+        F[2 * s] = F[2 * s + 1] = 0.0f;
+        DY[2 * s] = DY[2 * s + 1] = 0.0f;
+        LS[s] = 0.0f;
+        for (int i = 0; i < H; ++i) h1[i] = h2[i] = dz2[i] = dz1[i] = 0.0f;
+    }
+    __syncthreads();
+    float* out = g.partial + (int64_t)blockIdx.x * (NP + 1);
+    for (int q = threadIdx.x; q <= NP; q += blockDim.x) {
+        float acc = 0.0f;
+        if (q < OFF_B1) {                       // W1[i][c]
+            const int i = q / 2, c = q % 2;
+            for (int t = 0; t < kTrainBlock; ++t) acc = fmaf(DZ1[i * kPad + t], F[2 * t + c], acc);
+        } else if (q < OFF_W2) {                // b1[i]
+            const int i = q - OFF_B1;
+            for (int t = 0; t < kTrainBlock; ++t) acc += DZ1[i * kPad + t];
+        } else if (q < OFF_B2) {                // W2[j][i]
+            const int j = (q - OFF_W2) / H, i = (q - OFF_W2) % H;
+            for (int t = 0; t < kTrainBlock; ++t) acc = fmaf(DZ2[j * kPad + t], H1[i * kPad + t], acc);
+        } else if (q < OFF_W3) {                // b2[j]
+            const int j = q - OFF_B2;
+            for (int t = 0; t < kTrainBlock; ++t) acc += DZ2[j * kPad + t];
+        } else if (q < OFF_B3) {                // W3[k][j]
+            const int k = (q - OFF_W3) / H, j = (q - OFF_W3) % H;
+            for (int t = 0; t < kTrainBlock; ++t) acc = fmaf(DY[2 * t + k], H2[j * kPad + t], acc);
+        } else if (q < NP) {                    // b3[k]
+            const int k = q - OFF_B3;
+            for (int t = 0; t < kTrainBlock; ++t) acc += DY[2 * t + k];
+        } else {                                // loss share
+            for (int t = 0; t < kTrainBlock; ++t) acc += LS[t];
+            acc /= (float)g.batch;
+        }
+        out[q] = acc;
+    }
+}
+
+struct ReduceArgs {
+    const float* partial;
+    int nblocks;
+    float* params;
+    float* m;
+    float* s;
+    unsigned short* w2h;
+    int update;
+    float lr, beta1, beta2, eps;
+    float bc1, bc2;          // 1 - beta^t
+    float* loss_out;         // [1] slot for this step, or NULL
+    double* loss_d;          // or NULL
+    float* grads_out;        // [NP] or NULL
+};
+
+// Sum of the block partials (fixed order) and, optionally, the Adam update of every parameter.
+__global__ void mlp_reduce_kernel(ReduceArgs r)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q > NP) return;
+    double acc = 0.0;
+    for (int b = 0; b < r.nblocks; ++b) acc += (double)r.partial[(int64_t)b * (NP + 1) + q];
+    const float gq = (float)acc;
+    if (q == NP) {
+        if (r.loss_out) *r.loss_out = gq;
+        if (r.loss_d) *r.loss_d = acc;
+        return;
+    }
+    if (r.grads_out) r.grads_out[q] = gq;
+    if (!r.update) return;
+    const float m = r.beta1 * r.m[q] + (1.0f - r.beta1) * gq;
+    const float s = r.beta2 * r.s[q] + (1.0f - r.beta2) * gq * gq;
+    r.m[q] = m;
+    r.s[q] = s;
+    const float w = r.params[q] - r.lr * (m / r.bc1) / (sqrtf(s / r.bc2) + r.eps);
+    r.params[q] = w;
+    if (q >= OFF_W2 && q < OFF_B2) r.w2h[q - OFF_W2] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
+}
+
+size_t grad_smem_bytes() { return sizeof(float) * (NP + 2 + 5 * kTrainBlock + 4 * H * (kTrainBlock + 1)); }
+
+int run_grad(const kv_mlp* h, const double* v, const double* x, const double* t0,
+             const double* t1, int64_t n, int batch, int64_t step, uint64_t seed, int sequential,
+             float* partial, cudaStream_t s)
+{
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        KV_CUDA_TRY(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)grad_smem_bytes()));
+        attr_set[dev] = true;
+    }
+    GradArgs g;
+    g.params = h->params;
+    g.v = v;
+    g.x = x;
+    g.t0 = t0;
+    g.t1 = t1;
+    g.n = n;
+    g.batch = batch;
+    g.step = step;
+    g.seed = seed;
+    g.sequential = sequential;
+    g.partial = partial;
+    memcpy(g.in_scale, h->in_scale, sizeof(g.in_scale));
+    memcpy(g.out_scale, h->out_scale, sizeof(g.out_scale));
+    const int nb = (batch + kTrainBlock - 1) / kTrainBlock;
+    mlp_grad_kernel<<<nb, kTrainBlock, grad_smem_bytes(), s>>>(g);
+    KV_LAUNCH_CHECK();
+    return KV_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ library-internal hooks
 
 namespace kvh {
 
 int mlp_view(const kv_mlp* h, MlpView* out)
 {
-    (void)out;
-    return h ? KV_ERR_HANDLE : KV_ERR_HANDLE;
+    if (!valid(h)) return KV_ERR_HANDLE;
+    out->w1 = h->params + OFF_W1;
+    out->b1 = h->params + OFF_B1;
+    out->w2h = h->w2h;
+    out->b2 = h->params + OFF_B2;
+    out->w3 = h->params + OFF_W3;
+    out->b3 = h->params + OFF_B3;
+    memcpy(out->in_scale, h->in_scale, sizeof(out->in_scale));
+    memcpy(out->out_scale, h->out_scale, sizeof(out->out_scale));
+    return KV_OK;
 }
 
 int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter)
 {
-    (void)a;
-    (void)bins;
-    (void)log_eps;
-    (void)max_iter;
-    return KV_ERR_HANDLE;
+    if (a->n > (int64_t)0xffffffffll) return KV_ERR_SIZE;
+    MlpPathParams p;
+    int rc = mlp_view(a->mlp, &p.mlp);
+    if (rc != KV_OK) return rc;
+    p.v = (const float*)a->v;
+    p.x = (const float*)a->x;
+    p.logk = (float*)a->logk;
+    p.dv = (float*)a->dv;
+    p.dx = (float*)a->dx;
+    p.go = (const float*)a->grad_out;
+    p.status = a->status;
+    p.n = a->n;
+    p.bins = bins;
+    p.log_eps = (float)log_eps;
+    cudaStream_t s = (cudaStream_t)a->stream;
+    // scratch: the fallback list and its counter
+    uint32_t* scratch = nullptr;
+    KV_CUDA_TRY(cudaMallocAsync((void**)&scratch, sizeof(uint32_t) * (a->n + 32), s));
+    p.fb_count = scratch;
+    p.fb_list = scratch + 32;
+    cudaError_t e = cudaMemsetAsync(p.fb_count, 0, sizeof(uint32_t), s);
+    const bool deriv = a->dv || a->dx;
+    if (e == cudaSuccess) {
+        int per_sm = 0;
+        if (deriv)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kv_mlp_kernel<true>, kMlpBlock, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kv_mlp_kernel<false>, kMlpBlock, 0);
+        if (per_sm < 1) per_sm = 1;
+        int64_t need = (a->n + kMlpBlock - 1) / kMlpBlock;
+        int64_t cap = (int64_t)sm_count() * per_sm;
+        int grid = (int)(need < cap ? need : cap);
+        if (deriv) kv_mlp_kernel<true><<<grid, kMlpBlock, 0, s>>>(p);
+        else kv_mlp_kernel<false><<<grid, kMlpBlock, 0, s>>>(p);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        FallbackParams f;
+        f.p = p;
+        f.log_eps = log_eps;
+        f.max_iter = max_iter;
+        f.fallback_total = a->fallback_count;
+        int grid = sm_count() * 4;
+        if (deriv) kv_fallback_kernel<true><<<grid, kMlpBlock, 0, s>>>(f);
+        else kv_fallback_kernel<false><<<grid, kMlpBlock, 0, s>>>(f);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (e2 != cudaSuccess) return cuda_fail(e2);
+    return KV_OK;
 }
 
 }  // namespace kvh
 
+// ------------------------------------------------------------------ C ABI
+
 extern "C" {
-int kv_mlp_create(uint64_t, kv_mlp**) { return KV_ERR_HANDLE; }
-int kv_mlp_free(kv_mlp*) { return KV_OK; }
-int kv_mlp_save(const kv_mlp*, const char*) { return KV_ERR_HANDLE; }
-int kv_mlp_load(const char*, kv_mlp**) { return KV_ERR_HANDLE; }
-int kv_mlp_get_params(const kv_mlp*, float*, int64_t) { return KV_ERR_HANDLE; }
-int kv_mlp_set_params(kv_mlp*, const float*, int64_t) { return KV_ERR_HANDLE; }
-int kv_mlp_train(kv_mlp*, const kv_train_args*) { return KV_ERR_HANDLE; }
-int kv_mlp_loss_grad(const kv_mlp*, const double*, const double*, const double*, const double*,
-                     int64_t, double*, float*, void*)
+
+int kv_mlp_create(uint64_t seed, kv_mlp** out)
 {
-    return KV_ERR_HANDLE;
+    if (!out) return KV_ERR_NULL;
+    kv_mlp* h = nullptr;
+    int rc = alloc_handle(&h);
+    if (rc != KV_OK) return rc;
+    // He-uniform weights U(-sqrt(6/fan_in), sqrt(6/fan_in)) from SplitMix64, zero biases
+    std::vector<float> w(NP, 0.0f);
+    auto uni = [&](uint64_t k) { return (double)(mix64(seed * 0x100000001B3ull + k) >> 11) * 0x1.0p-53; };
+    for (int k = 0; k < 2 * H; ++k) w[OFF_W1 + k] = (float)((2 * uni(k) - 1) * sqrt(6.0 / 2.0));
+    for (int k = 0; k < H * H; ++k) w[OFF_W2 + k] = (float)((2 * uni(1000 + k) - 1) * sqrt(6.0 / H));
+    for (int k = 0; k < 2 * H; ++k) w[OFF_W3 + k] = (float)((2 * uni(10000 + k) - 1) * sqrt(6.0 / H));
+    rc = upload(h, w.data());
+    if (rc != KV_OK) {
+        kv_mlp_free(h);
+        return rc;
+    }
+    *out = h;
+    return KV_OK;
 }
-int kv_mlp_predict(const kv_mlp*, const void*, const void*, void*, void*, int64_t, int, void*)
+
+int kv_mlp_free(kv_mlp* h)
 {
-    return KV_ERR_HANDLE;
+    if (!h) return KV_OK;
+    if (h->magic != kMagic) return KV_ERR_HANDLE;
+    cudaFree(h->params);
+    cudaFree(h->adam_m);
+    cudaFree(h->adam_s);
+    cudaFree(h->w2h);
+    h->magic = 0;
+    delete h;
+    return KV_OK;
 }
+
+struct FileHeader {
+    char magic[8];
+    uint32_t version, hidden, nparams, reserved;
+    float in_scale[4], out_scale[4];
+    int64_t step;
+};
+
+int kv_mlp_save(const kv_mlp* h, const char* path)
+{
+    if (!valid(h)) return KV_ERR_HANDLE;
+    if (!path) return KV_ERR_NULL;
+    std::vector<float> buf(3 * NP);
+    KV_CUDA_TRY(cudaMemcpy(buf.data(), h->params, sizeof(float) * NP, cudaMemcpyDeviceToHost));
+    KV_CUDA_TRY(cudaMemcpy(buf.data() + NP, h->adam_m, sizeof(float) * NP, cudaMemcpyDeviceToHost));
+    KV_CUDA_TRY(cudaMemcpy(buf.data() + 2 * NP, h->adam_s, sizeof(float) * NP, cudaMemcpyDeviceToHost));
+    FileHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, "KVMLP1\0\0", 8);
+    hd.version = 1;
+    hd.hidden = H;
+    hd.nparams = NP;
+    memcpy(hd.in_scale, h->in_scale, sizeof(hd.in_scale));
+    memcpy(hd.out_scale, h->out_scale, sizeof(hd.out_scale));
+    hd.step = h->step;
+    FILE* f = fopen(path, "wb");
+    if (!f) return KV_ERR_IO;
+    bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1 && fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    ok = (fclose(f) == 0) && ok;
+    return ok ? KV_OK : KV_ERR_IO;
 }
+
+int kv_mlp_load(const char* path, kv_mlp** out)
+{
+    if (!path || !out) return KV_ERR_NULL;
+    FILE* f = fopen(path, "rb");
+    if (!f) return KV_ERR_IO;
+    FileHeader hd;
+    std::vector<float> buf(3 * NP);
+    bool ok = fread(&hd, sizeof(hd), 1, f) == 1;
+    if (ok && (memcmp(hd.magic, "KVMLP1\0\0", 8) != 0 || hd.version != 1 || hd.hidden != H ||
+               hd.nparams != NP)) {
+        fclose(f);
+        return KV_ERR_FORMAT;
+    }
+    ok = ok && fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    fclose(f);
+    if (!ok) return KV_ERR_FORMAT;
+    kv_mlp* h = nullptr;
+    int rc = alloc_handle(&h);
+    if (rc != KV_OK) return rc;
+    memcpy(h->in_scale, hd.in_scale, sizeof(hd.in_scale));
+    memcpy(h->out_scale, hd.out_scale, sizeof(hd.out_scale));
+    h->step = hd.step;
+    rc = upload(h, buf.data());
+    cudaError_t e = cudaSuccess;
+    if (rc == KV_OK) e = cudaMemcpy(h->adam_m, buf.data() + NP, sizeof(float) * NP, cudaMemcpyHostToDevice);
+    if (rc == KV_OK && e == cudaSuccess)
+        e = cudaMemcpy(h->adam_s, buf.data() + 2 * NP, sizeof(float) * NP, cudaMemcpyHostToDevice);
+    if (rc == KV_OK && e != cudaSuccess) rc = kvh::cuda_fail(e);
+    if (rc != KV_OK) {
+        kv_mlp_free(h);
+        return rc;
+    }
+    *out = h;
+    return KV_OK;
+}
+
+int kv_mlp_get_params(const kv_mlp* h, float* host_params, int64_t count)
+{
+    if (!valid(h)) return KV_ERR_HANDLE;
+    if (!host_params) return KV_ERR_NULL;
+    if (count != NP) return KV_ERR_SIZE;
+    KV_CUDA_TRY(cudaMemcpy(host_params, h->params, sizeof(float) * NP, cudaMemcpyDeviceToHost));
+    return KV_OK;
+}
+
+int kv_mlp_set_params(kv_mlp* h, const float* host_params, int64_t count)
+{
+    if (!valid(h)) return KV_ERR_HANDLE;
+    if (!host_params) return KV_ERR_NULL;
+    if (count != NP) return KV_ERR_SIZE;
+    KV_CUDA_TRY(cudaMemset(h->adam_m, 0, sizeof(float) * NP));
+    KV_CUDA_TRY(cudaMemset(h->adam_s, 0, sizeof(float) * NP));
+    h->step = 0;
+    return upload(h, host_params);
+}
+
+int kv_mlp_loss_grad(const kv_mlp* h, const double* v, const double* x, const double* t0,
+                     const double* t1, int64_t n, double* loss, float* grads, void* stream)
+{
+    if (!valid(h)) return KV_ERR_HANDLE;
+    if (n < 1 || n > (1 << 24)) return KV_ERR_SIZE;
+    if (!v || !x || !t0 || !t1 || !loss || !grads) return KV_ERR_NULL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nb = (int)((n + kTrainBlock - 1) / kTrainBlock);
+    float* partial = nullptr;
+    KV_CUDA_TRY(cudaMallocAsync((void**)&partial, sizeof(float) * (size_t)nb * (NP + 1), s));
+    int rc = run_grad(h, v, x, t0, t1, n, (int)n, 0, 0, 1, partial, s);
+    if (rc == KV_OK) {
+        ReduceArgs r;
+        memset(&r, 0, sizeof(r));
+        r.partial = partial;
+        r.nblocks = nb;
+        r.update = 0;
+        r.loss_d = loss;
+        r.grads_out = grads;
+        mlp_reduce_kernel<<<(NP + 1 + 127) / 128, 128, 0, s>>>(r);
+        kvh::note_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = kvh::cuda_fail(e);
+    }
+    cudaError_t e2 = cudaFreeAsync(partial, s);
+    if (rc == KV_OK && e2 != cudaSuccess) rc = kvh::cuda_fail(e2);
+    return rc;
+}
+
+int kv_mlp_train(kv_mlp* h, const kv_train_args* a)
+{
+    if (!valid(h)) return KV_ERR_HANDLE;
+    if (!a) return KV_ERR_NULL;
+    if (!a->v || !a->x || !a->t0 || !a->t1) return KV_ERR_NULL;
+    if (a->n < 1 || a->n > (int64_t)0xffffffffll) return KV_ERR_SIZE;
+    if (a->batch < 1 || a->batch > (1 << 20) || a->steps < 0) return KV_ERR_ARG;
+    if (!(a->lr > 0.0f) || !(a->beta1 >= 0.0f && a->beta1 < 1.0f) ||
+        !(a->beta2 >= 0.0f && a->beta2 < 1.0f) || !(a->adam_eps > 0.0f))
+        return KV_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)a->stream;
+    const int nb = (a->batch + kTrainBlock - 1) / kTrainBlock;
+    float* partial = nullptr;
+    KV_CUDA_TRY(cudaMallocAsync((void**)&partial, sizeof(float) * (size_t)nb * (NP + 1), s));
+    int rc = KV_OK;
+    for (int j = 0; j < a->steps && rc == KV_OK; ++j) {
+        const int64_t t = h->step + 1;
+        rc = run_grad(h, a->v, a->x, a->t0, a->t1, a->n, a->batch, h->step, a->seed, 0, partial, s);
+        if (rc != KV_OK) break;
+        ReduceArgs r;
+        memset(&r, 0, sizeof(r));
+        r.partial = partial;
+        r.nblocks = nb;
+        r.params = h->params;
+        r.m = h->adam_m;
+        r.s = h->adam_s;
+        r.w2h = h->w2h;
+        r.update = 1;
+        r.lr = a->lr;
+        r.beta1 = a->beta1;
+        r.beta2 = a->beta2;
+        r.eps = a->adam_eps;
+        r.bc1 = (float)(1.0 - pow((double)a->beta1, (double)t));
+        r.bc2 = (float)(1.0 - pow((double)a->beta2, (double)t));
+        r.loss_out = a->loss_out ? a->loss_out + j : nullptr;
+        mlp_reduce_kernel<<<(NP + 1 + 127) / 128, 128, 0, s>>>(r);
+        kvh::note_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = kvh::cuda_fail(e);
+        h->step = t;
+    }
+    cudaError_t e2 = cudaFreeAsync(partial, s);
+    if (rc == KV_OK && e2 != cudaSuccess) rc = kvh::cuda_fail(e2);
+    return rc;
+}
+
+int kv_mlp_predict(const kv_mlp* h, const void* v, const void* x, void* t0, void* t1, int64_t n,
+                   int dtype, void* stream)
+{
+    if (!valid(h)) return KV_ERR_HANDLE;
+    if (dtype != KV_MIXED) return KV_ERR_DTYPE;
+    if (n < 0) return KV_ERR_SIZE;
+    if (n == 0) return KV_OK;
+    if (!v || !x || !t0 || !t1) return KV_ERR_NULL;
+    kvh::MlpView m;
+    int rc = kvh::mlp_view(h, &m);
+    if (rc != KV_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t need = (n + kMlpBlock - 1) / kMlpBlock;
+    int64_t cap = (int64_t)kvh::sm_count() * 8;
+    int grid = (int)(need < cap ? need : cap);
+    kv_predict_kernel<<<grid, kMlpBlock, 0, s>>>(m, (const float*)v, (const float*)x, (float*)t0,
+                                                 (float*)t1, n);
+    KV_LAUNCH_CHECK();
+    return KV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,235 @@
+"""The learned bracket on the GPU: training kernels against the MLP oracle, checkpoints, and the
+fast path (MLP bracket, float-float offset, FP32 bins, plain fallback) against the method oracle.
+"""
+import os
+import tempfile
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle
+from conftest import rel, rel_logk
+from oracle import mlp as omlp
+from paper_2108_11560_gb300 import _native as N
+from paper_2108_11560_gb300 import kv, learned
+from paper_2108_11560_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0)
+TOL = 2e-6
+LOG_EPS = -20.0
+
+
+def _t(a, dtype=torch.float64):
+    return torch.tensor(np.asarray(a), dtype=dtype, device=DEV)
+
+
+def _np(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def _synthetic_targets(v, x, seed):
+    """A bracket around the exact peak with random widths (any targets serve a gradient check)."""
+    rng = np.random.default_rng(seed)
+    tp = omlp.peak(v, x)
+    t0 = np.maximum(tp - rng.uniform(0.01, 2.0, v.size), 0.0)
+    t1 = tp + rng.uniform(0.01, 4.0, v.size)
+    return t0, t1
+
+
+@pytest.fixture(scope="module")
+def net():
+    return learned.default_network(DEV)
+
+
+def test_loss_and_gradient_match_oracle():
+    v, x = W.learned_bracket(3000, seed=301)
+    v = v.astype(np.float32).astype(np.float64)
+    x = x.astype(np.float32).astype(np.float64)
+    t0, t1 = _synthetic_targets(v, x, 302)
+    p = np.random.default_rng(303).normal(0, 0.2, N.KV_MLP_NPARAMS).astype(np.float32)
+    m = learned.Mlp.create(0)
+    m.set_params(p)
+    assert np.array_equal(m.params(), p)
+    loss, g = m.loss_grad(_t(v), _t(x), _t(t0), _t(t1))
+    ref_loss, ref_g = omlp.loss_grad(p.astype(np.float64), v, x, t0, omlp.peak(v, x), t1)
+    assert abs(loss - ref_loss) <= 1e-5 * ref_loss
+    assert np.max(np.abs(g - ref_g)) <= 1e-4 * np.max(np.abs(ref_g))
+
+
+def test_adam_steps_match_oracle():
+    """Five Adam steps through the library's kernels (same SplitMix64 batches) against the
+    oracle's training loop."""
+    v, x = W.learned_bracket(4096, seed=304)
+    v = v.astype(np.float32).astype(np.float64)
+    x = x.astype(np.float32).astype(np.float64)
+    t0, t1 = _synthetic_targets(v, x, 305)
+    p = np.random.default_rng(306).normal(0, 0.2, N.KV_MLP_NPARAMS).astype(np.float32)
+    m = learned.Mlp.create(0)
+    m.set_params(p)
+    lr = 1e-3
+    losses = m.train(_t(v), _t(x), _t(t0), _t(t1), steps=5, batch=512, lr=lr, seed=7)
+    ref_p, ref_losses = omlp.train(p.astype(np.float64), v, x, t0, t1, steps=5, batch=512, lr=lr,
+                                   beta1=0.9, beta2=0.999, eps=1e-8, seed=7)
+    assert np.allclose(losses, ref_losses, rtol=1e-4)
+    d = np.abs(m.params() - ref_p)
+    # Adam normalises each step to about lr: agreement far below lr except where a gradient
+    # component is at rounding level and its sign is arbitrary
+    assert np.quantile(d, 0.99) < 0.01 * lr
+    assert d.max() < 10 * lr
+
+
+def test_checkpoint_roundtrip(net):
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "net.kvmlp")
+        net.save(path)
+        back = learned.Mlp.load(path)
+        assert np.array_equal(back.params(), net.params())
+        v, x = W.learned_bracket(1000, seed=307)
+        vf, xf = _t(v, torch.float32), _t(x, torch.float32)
+        a0, a1 = net.predict(vf, xf)
+        b0, b1 = back.predict(vf, xf)
+        assert torch.equal(a0, b0) and torch.equal(a1, b1)
+        with open(path, "r+b") as f:
+            f.write(b"XXXXXXXX")
+        with pytest.raises(N.KvError):
+            learned.Mlp.load(path)
+
+
+def test_predictions_match_oracle_forward(net):
+    """The inference kernel (BF16 W2 and hidden units, FP32 accumulation) against the oracle's
+    float64 forward pass on the same FP32 parameters, in the log half-widths."""
+    v, x = W.learned_bracket(4000, seed=308)
+    v = v.astype(np.float32).astype(np.float64)
+    x = x.astype(np.float32).astype(np.float64)
+    t0, t1 = net.predict(_t(v, torch.float32), _t(x, torch.float32))
+    tp = omlp.peak(v, x)
+    r0, r1 = omlp.predict(net.params().astype(np.float64), v, x, tp)
+    L = lambda a: np.log(np.maximum(a, 0) + omlp.DELTA)
+    # BF16 rounding of W2 and h1: a few parts in 1e3 of the outputs' scale (more in the log of a
+    # small left width, where a small shift of t0 is a large relative change)
+    e1 = np.abs(L(_np(t1) - tp) - L(r1 - tp))
+    assert np.quantile(e1, 0.99) < 0.02 and e1.max() < 0.1
+    sel = (_np(t0) > 0) & (r0 > 0)  # both sides unclamped
+    e0 = np.abs(L(tp[sel] - _np(t0)[sel]) - L(tp[sel] - r0[sel]))
+    assert np.quantile(e0, 0.99) < 0.03 and e0.max() < 0.3
+
+
+def test_trained_network_fits_its_targets(net):
+    """After training, the predicted log half-widths are within a few percent of the plain
+    bracket's on fresh pairs of the training distribution."""
+    v, x, t0, t1 = learned.training_set(DEV, n=20000, seed=309)
+    p0, p1 = net.predict(v.float(), x.float())
+    tp = omlp.peak(_np(v), _np(x))
+    L = lambda a: np.log(np.maximum(a, 0) + omlp.DELTA)
+    e1 = np.abs(L(_np(p1) - tp) - L(_np(t1) - tp))
+    assert np.median(e1) < 0.03 and np.quantile(e1, 0.99) < 0.2
+
+
+@pytest.mark.parametrize("bins", [32, 40])
+def test_mlp_path_matches_oracle(net, bins):
+    """The fast path on the hard-band and learned-bracket workloads against the oracle's method
+    (FP64 ... long double) and the dense truth; every pair, fallback or not."""
+    v1, x1 = W.hard_band(20000, seed=310)
+    v2, x2 = W.learned_bracket(20000, seed=311)
+    v = np.concatenate([v1, v2, [0.0, 0.5, 200.0, 3.0]])
+    x = np.concatenate([x1, x2, [1e-4, 1.0, 1e-4, 1e4]])
+    (vf, v64), (xf, x64) = W.to_f32(v, x)
+    fb = torch.zeros(1, dtype=torch.int64, device=DEV)
+    out = kv.kv_fwd_bwd_ex(_t(vf, torch.float32), _t(xf, torch.float32), bins=bins, bracket="mlp",
+                           mlp=net, status=True, fallback_count=fb)
+    lk, dv, dx = _np(out["logk"]), _np(out["dv"]), _np(out["dx"])
+    st = out["status"].cpu().numpy()
+    ref = oracle.o1(v64, x64, bins=bins, log_eps=LOG_EPS, precision="long")
+    assert rel_logk(lk, ref["logk"]).max() < TOL
+    z = v64 == 0
+    assert np.all(dv[z] == 0)
+    assert rel(dv[~z], ref["dv"][~z]).max() < TOL
+    assert rel(dx, ref["dx"]).max() < TOL
+    n_fb = int(np.count_nonzero(st & N.KV_PAIR_FALLBACK))
+    assert fb.item() == n_fb
+    assert n_fb < 0.02 * v.size, n_fb / v.size
+    truth = oracle.dense(v64[::10], x64[::10])
+    assert rel_logk(lk[::10], truth["logk"]).max() < TOL
+    assert rel(dx[::10], truth["dx"]).max() < TOL
+
+
+def test_fallback_path_is_exact_enough():
+    """A network that predicts nothing useful sends (almost) every pair to the plain-bracket
+    fallback, whose results still meet the tolerance."""
+    bad = learned.Mlp.create(5)  # untrained
+    v, x = W.hard_band(8000, seed=312)
+    (vf, v64), (xf, x64) = W.to_f32(v, x)
+    fb = torch.zeros(1, dtype=torch.int64, device=DEV)
+    out = kv.kv_fwd_bwd_ex(_t(vf, torch.float32), _t(xf, torch.float32), bins=32, bracket="mlp",
+                           mlp=bad, status=True, fallback_count=fb)
+    st = out["status"].cpu().numpy()
+    assert fb.item() == np.count_nonzero(st & N.KV_PAIR_FALLBACK) > 0.5 * v.size
+    ref = oracle.o1(v64, x64, bins=32, log_eps=LOG_EPS, precision="long")
+    assert rel_logk(_np(out["logk"]), ref["logk"]).max() < TOL
+    assert rel(_np(out["dx"]), ref["dx"]).max() < TOL
+
+
+def test_mlp_path_edge_cases(net):
+    v = np.array([1.0, 0.0, -2.0, 3.0, -3.0, np.inf, -np.inf, 1.0, np.nan, 1.0, 0.0, -2.5])
+    x = np.array([0.0, 0.0, 0.0, np.inf, np.inf, 1.0, 1.0, -1.0, 1.0, np.nan, np.inf, 3.0])
+    out = kv.kv_fwd_bwd_ex(_t(v, torch.float32), _t(x, torch.float32), bracket="mlp", mlp=net,
+                           status=True)
+    ref = oracle.o1(v, x, precision="long")
+    for k in ("logk", "dv", "dx"):
+        g = _np(out[k])
+        r = ref[k]
+        both_nan = np.isnan(g) & np.isnan(r)
+        close = np.isfinite(r) & (np.abs(g - np.nan_to_num(r)) <= 2e-6 * np.maximum(1, np.abs(np.nan_to_num(r))))
+        assert np.all(both_nan | (g == r) | close), (k, g, r)
+    st = out["status"].cpu().numpy()
+    assert np.all(st[:11] == N.KV_PAIR_EDGE) and not (st[11] & N.KV_PAIR_EDGE)
+
+
+def test_mlp_path_full_size_sampled(net):
+    """The bench's launch: 16,777,216 hard-band pairs, fast path at 32 bins, sampled check."""
+    n = 16_777_216
+    v, x = W.hard_band(n, seed=1)
+    (vf, v64), (xf, x64) = W.to_f32(v, x)
+    fb = torch.zeros(1, dtype=torch.int64, device=DEV)
+    out = kv.kv_fwd_bwd_ex(_t(vf, torch.float32), _t(xf, torch.float32), bins=32, bracket="mlp",
+                           mlp=net, fallback_count=fb)
+    for k in ("logk", "dv", "dx"):
+        assert torch.isfinite(out[k]).all()
+    assert fb.item() < 0.01 * n
+    idx = np.random.default_rng(313).choice(n, 4096, replace=False)
+    ref = oracle.o1(v64[idx], x64[idx], bins=32, log_eps=LOG_EPS, precision="long")
+    assert rel_logk(_np(out["logk"])[idx], ref["logk"]).max() < TOL
+    assert rel(_np(out["dx"])[idx], ref["dx"]).max() < TOL
+    z = v64[idx] == 0
+    assert rel(_np(out["dv"])[idx][~z], ref["dv"][~z]).max() < TOL
+
+
+def test_learned_bracket_gain(net):
+    """What the trained network gains: the fast path against the same mixed path with the plain
+    FP64 bracket on the same 4M pairs (and the same accuracy bar, checked above)."""
+    n = 1 << 22
+    v, x = W.hard_band(n, seed=314)
+    vt, xt = _t(v, torch.float32), _t(x, torch.float32)
+
+    def timed(**kw):
+        for _ in range(2):
+            kv.kv_fwd_bwd_ex(vt, xt, bins=32, **kw)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(3):
+            kv.kv_fwd_bwd_ex(vt, xt, bins=32, **kw)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) / 3
+
+    t_plain = timed(bracket="plain")
+    t_mlp = timed(bracket="mlp", mlp=net)
+    print(f"plain bracket {n / t_plain:.3e} pairs/s, learned bracket {n / t_mlp:.3e} pairs/s")
+    assert t_mlp < 0.5 * t_plain

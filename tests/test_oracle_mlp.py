@@ -23,7 +23,7 @@ def _batch(n, seed):
 
 
 def test_gradient_matches_central_differences():
-    """Every one of the 4418 partial derivatives against a central difference of the loss."""
+    """Every one of the 4482 partial derivatives against a central difference of the loss."""
     p = _rand_params(1)
     v, x, t0, tp, t1 = _batch(24, 2)
     _, g = mlp.loss_grad(p, v, x, t0, tp, t1)
@@ -101,6 +101,24 @@ def test_training_reduces_loss():
     t0 = np.maximum(tp - 1.0 / np.sqrt(1 + x), 0)
     t1 = tp + 3.0 / np.sqrt(1 + x)
     p0 = _rand_params(9, 0.2)
-    p, losses = mlp.train(p0, v, x, t0, tp, t1, steps=300, batch=256, lr=3e-3, beta1=0.9,
+    p, losses = mlp.train(p0, v, x, t0, t1, steps=300, batch=256, lr=3e-3, beta1=0.9,
                           beta2=0.999, eps=1e-8, seed=10)
     assert losses[-20:].mean() < 0.2 * losses[:5].mean()
+
+
+def test_peak_is_the_zero_of_g_prime():
+    """The reference point of the learned bracket: the zero of g' (brentq), 0 when v^2 <= x."""
+    import scipy.optimize
+
+    import oracle
+    rng = np.random.default_rng(11)
+    v = np.concatenate([rng.uniform(0, 1000, 150), [1.0, 2.0, 0.0]])
+    x = np.concatenate([10 ** rng.uniform(-6, 5, 150), [1.0, 3.99, 1.0]])
+    t = mlp.peak(v, x)
+    for i in range(v.size):
+        if v[i] ** 2 <= x[i]:
+            assert t[i] == 0
+            continue
+        g = lambda s: oracle.g_eval(v[i], x[i], [s], precision="long")[1][0]
+        root = scipy.optimize.brentq(g, 1e-300, 64.0, xtol=1e-15)
+        assert abs(t[i] - root) <= 1e-9 * max(1.0, root)
