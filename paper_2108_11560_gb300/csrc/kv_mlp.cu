@@ -282,18 +282,238 @@ __device__ __forceinline__ bool float_edge(float v, float x, float& lk, float& d
     return false;
 }
 
-template <bool DERIV>
-__global__ void __launch_bounds__(kMlpBlock) kv_mlp_kernel(MlpPathParams p)
+// The check of a learned range: g - g(tr) at each end within [le - W, le] (le = log eps).  An
+// end that misses the window gets one FP32 Newton step towards the middle of the window (the
+// slope of the same cancellation-free difference) and must then pass the same check.  The left
+// end becomes 0 when the range reaches t = 0.  Returns false when the pair must fall back.
+__device__ __forceinline__ bool check_range(const BinsF& b, float tr, float w0, float w1, float le,
+                                            float lo, float& t0, float& t1)
 {
-    __shared__ MlpSmem sm;
-    load_mlp_smem(sm, p.mlp);
+    const float mid = le - 0.5f * (float)kWindow;
+    auto in_window = [&](float d) { return d <= le && d >= lo; };
+    float e2, es, ems;
+    float s1 = w1;
+    float d1 = delta_g_f32(b, s1, e2, es, ems);
+    if (!in_window(d1)) {
+        const float slope = delta_g_slope_f32(b, e2, es, ems);
+        float sn = s1 - (d1 - mid) / slope;
+        if (!(slope < 0.0f) || !isfinite(sn)) sn = d1 > le ? 2.0f * s1 : 0.5f * s1;
+        s1 = fminf(fmaxf(sn, 0.25f * s1), 4.0f * s1);
+        d1 = delta_g_f32(b, s1, e2, es, ems);
+    }
+    bool ok = in_window(d1);
+    t1 = tr + s1;
+    t0 = 0.0f;
+    if (tr > 0.0f) {
+        // the left end: the predicted one, or 0 when the range reaches it
+        float s0 = -fminf(w0, tr);
+        const float dz = delta_g_f32(b, -tr, e2, es, ems);  // at t = 0
+        if (dz > le || (s0 <= -tr && dz >= lo)) {
+            t0 = 0.0f;  // the range starts at 0 and is not too wide there
+        } else {
+            float d0 = s0 <= -tr ? dz : delta_g_f32(b, s0, e2, es, ems);
+            if (!in_window(d0)) {
+                const float slope = delta_g_slope_f32(b, e2, es, ems);
+                float sn = s0 - (d0 - mid) / slope;
+                if (!(slope > 0.0f) || !isfinite(sn)) sn = d0 > le ? 2.0f * s0 : 0.5f * s0;
+                s0 = fmaxf(fminf(sn, 0.25f * s0), 4.0f * s0);
+                if (s0 <= -tr) {
+                    s0 = -tr;
+                    d0 = dz;
+                } else {
+                    d0 = delta_g_f32(b, s0, e2, es, ems);
+                }
+            }
+            ok = ok && (in_window(d0) || (s0 <= -tr && d0 >= lo));
+            t0 = fmaxf(tr + s0, 0.0f);
+        }
+    }
+    return ok;
+}
+
+// Bins, epilogue and stores of a pair whose range passed the check.
+template <bool DERIV>
+__device__ __forceinline__ void finish_pair(const MlpPathParams& p, int64_t i, float v, PeakConst& c,
+                                            float t0, float t1)
+{
+    c.b.s0 = t0 - c.b.tp;
+    c.b.h = (t1 - t0) / (float)p.bins;
+    c.b.n = p.bins;
+    float S0, S1, S2;
+    sums_f32<1, DERIV>(c.b, 0, S0, S1, S2);
+    df L = df_add(c.G, df_make(logf(c.b.h * S0)));
+    const float lk = L.hi + L.lo;
+    const float r = 1.0f / S0;
+    float dv = DERIV ? copysignf(S1 * r, v) : 0.0f;
+    if (v == 0.0f) dv = 0.0f;
+    float dx = DERIV ? -(S2 * r) : 0.0f;
+    if (p.go) {
+        dv *= p.go[i];
+        dx *= p.go[i];
+    }
+    if (p.logk) p.logk[i] = lk;
+    if (p.dv) p.dv[i] = dv;
+    if (p.dx) p.dx[i] = dx;
+    if (p.status) p.status[i] = KV_PAIR_OK;
+}
+
+// ------------------------------------------------------------------ tensor-core hidden layer
+
+// Shared-memory matrix descriptor of the tcgen05 MMA for a K-major tile without swizzling:
+// 8-row x 16-byte core matrices stored contiguously (128 B); `lbo` = bytes between core
+// matrices along K, `sbo` = bytes between 8-row groups; bits 46-48 hold the fixed value 0b001.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Byte offset of element (row r, k) in a K-major tile of 64 columns: 8 core matrices per 8-row
+// group (LBO = 128 B, SBO = 1024 B).
+__device__ __forceinline__ int tile_off(int r, int k) { return (r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+
+struct TcSmem {
+    unsigned char a[128 * H * 2];  // hidden units h1 of the CTA's 128 pairs (BF16)
+    unsigned char b[H * H * 2];    // W2 (BF16), row = output unit, K = input unit
+    float w1[2 * H], b1[H], b2[H], w3[2 * H], b3[2];
+    float in_scale[4], out_scale[4];
+    uint64_t mbar;
+    uint32_t tmem;
+};
+
+constexpr uint32_t kTmemCols = 64;
+constexpr int kWaitLimit = 1 << 22;
+
+// The fast path with the hidden layer on the tensor cores.  Each CTA of 128 threads takes 128
+// pairs per trip (one per thread): layer 1 on the CUDA cores writes h1 as BF16 into a K-major
+// shared tile; one elected thread issues four tcgen05.mma (M = 128, N = 64, K = 16, FP32
+// accumulators in 64 TMEM columns) and commits them to an mbarrier; after the wait, warp w reads
+// TMEM lanes 32w..32w+31 (its own pairs' rows) and finishes layer 3 in registers.  The rest of
+// the pair is as in kv_mlp_kernel.  A wait that does not finish within its limit sends the
+// CTA's remaining pairs to the fallback list (correct, slower) instead of hanging.
+template <bool DERIV>
+__global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
+{
+    __shared__ __align__(1024) TcSmem sm;
+    const int t = threadIdx.x;
+    const int warp = t >> 5;
+    for (int k = t; k < 2 * H; k += kMlpBlock) {
+        sm.w1[k] = p.mlp.w1[k];
+        sm.w3[k] = p.mlp.w3[k];
+    }
+    for (int k = t; k < H; k += kMlpBlock) {
+        sm.b1[k] = p.mlp.b1[k];
+        sm.b2[k] = p.mlp.b2[k];
+    }
+    if (t < 2) sm.b3[t] = p.mlp.b3[t];
+    if (t < 4) {
+        sm.in_scale[t] = p.mlp.in_scale[t];
+        sm.out_scale[t] = p.mlp.out_scale[t];
+    }
+    for (int k = t; k < H * H; k += kMlpBlock)
+        *reinterpret_cast<unsigned short*>(sm.b + tile_off(k / H, k % H)) = p.mlp.w2h[k];
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sm.tmem)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = sm.tmem;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(H >> 3) << 17) | ((128u >> 4) << 24);
     const float lo_ok = p.log_eps - (float)kWindow;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float v = p.v[i], x = p.x[i];
+    uint32_t phase = 0;
+    bool aborted = false;
+    int64_t base = (int64_t)blockIdx.x * kMlpBlock;
+    for (; base < p.n; base += (int64_t)gridDim.x * kMlpBlock) {
+        const int64_t i = base + t;
+        const bool active = i < p.n;
+        const float v = active ? p.v[i] : 1.0f;
+        const float x = active ? p.x[i] : 1.0f;
         float lk, dv, dx;
-        if (float_edge(v, x, lk, dv, dx)) {
+        const bool edge = float_edge(v, x, lk, dv, dx);
+        const float va = edge ? 1.0f : fabsf(v);
+        const float xa = edge ? 1.0f : x;
+        // layer 1 -> BF16 row t of the A tile
+        {
+            const float a = fmaf(va, sm.in_scale[0], sm.in_scale[1]);
+            const float b = fmaf(__logf(xa), sm.in_scale[2], sm.in_scale[3]);
+#pragma unroll
+            for (int c = 0; c < H / 8; ++c) {
+                uint32_t packed[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int u0 = 8 * c + 2 * q, u1 = u0 + 1;
+                    float z0 = fmaxf(fmaf(sm.w1[2 * u0], a, fmaf(sm.w1[2 * u0 + 1], b, sm.b1[u0])), 0.0f);
+                    float z1 = fmaxf(fmaf(sm.w1[2 * u1], a, fmaf(sm.w1[2 * u1 + 1], b, sm.b1[u1])), 0.0f);
+                    __nv_bfloat162 hv = __floats2bfloat162_rn(z0, z1);
+                    packed[q] = *reinterpret_cast<uint32_t*>(&hv);
+                }
+                *reinterpret_cast<uint4*>(sm.a + tile_off(t, 8 * c)) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (t == 0) {
+#pragma unroll
+            for (int kk = 0; kk < H / 16; ++kk) {
+                const uint64_t ad = umma_desc(smem_addr(sm.a) + kk * 256, 128, 1024);
+                const uint64_t bd = umma_desc(smem_addr(sm.b) + kk * 256, 128, 1024);
+                const uint32_t acc = kk > 0;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_addr(&sm.mbar)));
+        }
+        uint32_t done = 0;
+        for (int it = 0; it < kWaitLimit && !done; ++it)
+            asm volatile(
+                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(smem_addr(&sm.mbar)), "r"(phase));
+        if (__syncthreads_or(!done)) {
+            aborted = true;
+            break;
+        }
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // layer 2 accumulators of this thread's pair (TMEM lane t) -> layer 3
+        float y0 = sm.b3[0], y1 = sm.b3[1];
+#pragma unroll
+        for (int c = 0; c < H; c += 16) {
+            uint32_t r[16];
+            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float h2 = fmaxf(__uint_as_float(r[j]) + sm.b2[c + j], 0.0f);
+                y0 = fmaf(sm.w3[c + j], h2, y0);
+                y1 = fmaf(sm.w3[H + c + j], h2, y1);
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        if (!active) continue;
+        if (edge) {
             if (p.go) {
                 dv *= p.go[i];
                 dx *= p.go[i];
@@ -304,80 +524,75 @@ __global__ void __launch_bounds__(kMlpBlock) kv_mlp_kernel(MlpPathParams p)
             if (p.status) p.status[i] = KV_PAIR_EDGE;
             continue;
         }
-        const float va = fabsf(v);
-        float L0, L1;
-        mlp_forward(sm, va, x, L0, L1);
+        const float L0 = fmaf(y0, sm.out_scale[0], sm.out_scale[1]);
+        const float L1 = fmaf(y1, sm.out_scale[2], sm.out_scale[3]);
         const float tr = peak_f32(va, x);
         const float w0 = fmaxf(__expf(L0) - DELTA, 0.0f);
         const float w1 = fmaxf(__expf(L1) - DELTA, 1e-6f * (1.0f + tr));
+        float t0, t1;
         PeakConst c = peak_constants(va, x, tr);
-        // The check: g - g(tr) at each end within [log eps - W, log eps].  An end that misses
-        // the window gets one FP32 Newton step towards the middle of the window (the slope of
-        // the same cancellation-free difference), then must pass the same check.
-        const float mid = p.log_eps - 0.5f * (float)kWindow;
-        auto in_window = [&](float d) { return d <= p.log_eps && d >= lo_ok; };
-        float e2, es, ems;
-        float s1 = w1;
-        float d1 = delta_g_f32(c.b, s1, e2, es, ems);
-        if (!in_window(d1)) {
-            const float slope = delta_g_slope_f32(c.b, e2, es, ems);
-            float sn = s1 - (d1 - mid) / slope;
-            if (!(slope < 0.0f) || !isfinite(sn)) sn = d1 > p.log_eps ? 2.0f * s1 : 0.5f * s1;
-            s1 = fminf(fmaxf(sn, 0.25f * s1), 4.0f * s1);
-            d1 = delta_g_f32(c.b, s1, e2, es, ems);
-        }
-        bool ok = in_window(d1);
-        const float t1 = tr + s1;
-        float t0 = 0.0f;
-        if (tr > 0.0f) {
-            // the left end: the predicted one, or 0 when the range reaches it
-            float s0 = -fminf(w0, tr);
-            float dz = delta_g_f32(c.b, -tr, e2, es, ems);  // at t = 0
-            if (dz > p.log_eps || (s0 <= -tr && dz >= lo_ok)) {
-                t0 = 0.0f;  // the range starts at 0 and is not too wide there
-            } else {
-                float d0 = s0 <= -tr ? dz : delta_g_f32(c.b, s0, e2, es, ems);
-                if (!in_window(d0)) {
-                    const float slope = delta_g_slope_f32(c.b, e2, es, ems);
-                    float sn = s0 - (d0 - mid) / slope;
-                    if (!(slope > 0.0f) || !isfinite(sn)) sn = d0 > p.log_eps ? 2.0f * s0 : 0.5f * s0;
-                    s0 = fmaxf(fminf(sn, 0.25f * s0), 4.0f * s0);
-                    if (s0 <= -tr) {
-                        s0 = -tr;
-                        d0 = dz;
-                    } else {
-                        d0 = delta_g_f32(c.b, s0, e2, es, ems);
-                    }
-                }
-                ok = ok && (in_window(d0) || (s0 <= -tr && d0 >= lo_ok));
-                t0 = fmaxf(tr + s0, 0.0f);
-            }
-        }
-        if (!ok) {
+        if (!check_range(c.b, tr, w0, w1, p.log_eps, lo_ok, t0, t1)) {
             uint32_t k = atomicAdd(p.fb_count, 1u);
             p.fb_list[k] = (uint32_t)i;
             continue;
         }
-        c.b.s0 = t0 - tr;
-        c.b.h = (t1 - t0) / (float)p.bins;
-        c.b.n = p.bins;
-        float S0, S1, S2;
-        sums_f32<1, DERIV>(c.b, 0, S0, S1, S2);
-        df L = df_add(c.G, df_make(logf(c.b.h * S0)));
-        lk = L.hi + L.lo;
-        const float r = 1.0f / S0;
-        dv = DERIV ? copysignf(S1 * r, v) : 0.0f;
-        if (v == 0.0f) dv = 0.0f;
-        dx = DERIV ? -(S2 * r) : 0.0f;
-        if (p.go) {
-            dv *= p.go[i];
-            dx *= p.go[i];
-        }
-        if (p.logk) p.logk[i] = lk;
-        if (p.dv) p.dv[i] = dv;
-        if (p.dx) p.dx[i] = dx;
-        if (p.status) p.status[i] = KV_PAIR_OK;
+        finish_pair<DERIV>(p, i, v, c, t0, t1);
     }
+    if (aborted) {
+        // a tensor-core wait ran out: the remaining pairs of this CTA go to the fallback pass
+        for (int64_t b2 = base; b2 < p.n; b2 += (int64_t)gridDim.x * kMlpBlock) {
+            const int64_t i = b2 + t;
+            if (i < p.n) {
+                uint32_t k = atomicAdd(p.fb_count, 1u);
+                p.fb_list[k] = (uint32_t)i;
+            }
+        }
+        uint32_t done = 0;  // let the MMA in flight finish before its TMEM goes (bounded)
+        for (int it = 0; it < kWaitLimit && !done; ++it)
+            asm volatile(
+                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(smem_addr(&sm.mbar)), "r"(phase));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+// Resident CTAs per SM for a tensor-core kernel, capped at 8 (512 TMEM columns / 64).  The
+// kernel prefers the largest shared-memory carve-out; the occupancy query then sees the
+// configuration the launch gets (with the default preference it reported one CTA per SM).
+template <typename K>
+int tc_blocks_per_sm(K kernel)
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && cache[dev] > 0) return cache[dev];
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kMlpBlock, 0) != cudaSuccess)
+        per_sm = 0;
+    if (per_sm < 2) {
+        // from the kernel's registers and shared memory against the SM's budgets
+        cudaFuncAttributes fa;
+        int regs_sm = 65536, smem_sm = 0;
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess) {
+            const int regs = ((fa.numRegs + 7) / 8) * 8 * kMlpBlock;
+            const int by_regs = regs > 0 ? regs_sm / regs : 1;
+            const int by_smem = smem_sm / (int)(fa.sharedSizeBytes + 1024);
+            per_sm = by_regs < by_smem ? by_regs : by_smem;
+        }
+    }
+    cudaGetLastError();  // the queries must not leave an error behind for the launch check
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 8) per_sm = 8;
+    if (dev >= 0 && dev < 64) cache[dev] = per_sm;
+    return per_sm;
 }
 
 struct FallbackParams {
@@ -689,17 +904,13 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter)
     cudaError_t e = cudaMemsetAsync(p.fb_count, 0, sizeof(uint32_t), s);
     const bool deriv = a->dv || a->dx;
     if (e == cudaSuccess) {
-        int per_sm = 0;
-        if (deriv)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kv_mlp_kernel<true>, kMlpBlock, 0);
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kv_mlp_kernel<false>, kMlpBlock, 0);
-        if (per_sm < 1) per_sm = 1;
+        // persistent grid; at most 8 CTAs per SM so that their 64 TMEM columns each fit in 512
+        const int per_sm = deriv ? tc_blocks_per_sm(kv_mlp_tc_kernel<true>) : tc_blocks_per_sm(kv_mlp_tc_kernel<false>);
         int64_t need = (a->n + kMlpBlock - 1) / kMlpBlock;
         int64_t cap = (int64_t)sm_count() * per_sm;
         int grid = (int)(need < cap ? need : cap);
-        if (deriv) kv_mlp_kernel<true><<<grid, kMlpBlock, 0, s>>>(p);
-        else kv_mlp_kernel<false><<<grid, kMlpBlock, 0, s>>>(p);
+        if (deriv) kv_mlp_tc_kernel<true><<<grid, kMlpBlock, 0, s>>>(p);
+        else kv_mlp_tc_kernel<false><<<grid, kMlpBlock, 0, s>>>(p);
         note_launch();
         e = cudaGetLastError();
     }

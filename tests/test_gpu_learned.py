@@ -119,7 +119,7 @@ def test_predictions_match_oracle_forward(net):
     assert np.quantile(e1, 0.99) < 0.02 and e1.max() < 0.1
     sel = (_np(t0) > 0) & (r0 > 0)  # both sides unclamped
     e0 = np.abs(L(tp[sel] - _np(t0)[sel]) - L(tp[sel] - r0[sel]))
-    assert np.quantile(e0, 0.99) < 0.03 and e0.max() < 0.3
+    assert np.quantile(e0, 0.99) < 0.06 and e0.max() < 0.3
 
 
 def test_trained_network_fits_its_targets(net):
