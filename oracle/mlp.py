@@ -3,7 +3,7 @@
 The network maps (v, log x) to the range [t0, t1] of Sec. 2.3 (the range the plain bracket of
 Algorithms 1-3 finds).  Layout and arithmetic, written out plainly:
 
-  features   a = v * IN_SCALE[0] + IN_SCALE[1],   b = ln(x) * IN_SCALE[2] + IN_SCALE[3]
+  features   a = asinh(v * IN_SCALE[0]) * IN_SCALE[1],   b = ln(x) * IN_SCALE[2] + IN_SCALE[3]
   layer 1    h1 = relu(W1 [a, b] + b1)                     W1: 64 x 2
   layer 2    h2 = relu(W2 h1 + b2)                         W2: 64 x 64
   layer 3    y  = W3 h2 + b3                               W3: 2 x 64
@@ -27,7 +27,7 @@ import numpy as np
 
 H = 64
 NPARAMS = H * 2 + H + H * H + H + 2 * H + 2
-IN_SCALE = (1.0 / 100.0, -1.0, 1.0 / (4.0 * math.log(10.0)), 0.0)
+IN_SCALE = (2.0, 2.0 / math.asinh(400.0), 1.0 / (4.0 * math.log(10.0)), 0.0)
 OUT_SCALE = (3.0, -3.0, 2.0, -1.0)  # (scale, shift) of L_0, then of L_1
 DELTA = 1e-3
 MASK64 = (1 << 64) - 1
@@ -54,7 +54,8 @@ def pack(d):
 def features(v, x):
     v = np.asarray(v, dtype=np.float64)
     x = np.asarray(x, dtype=np.float64)
-    return np.stack([v * IN_SCALE[0] + IN_SCALE[1], np.log(x) * IN_SCALE[2] + IN_SCALE[3]], axis=1)
+    return np.stack([np.arcsinh(v * IN_SCALE[0]) * IN_SCALE[1], np.log(x) * IN_SCALE[2] + IN_SCALE[3]],
+                    axis=1)
 
 
 def forward(p, v, x):

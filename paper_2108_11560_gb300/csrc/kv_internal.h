@@ -39,7 +39,7 @@ struct MlpView {
     const float* b2;            // [64]
     const float* w3;            // [2][64]
     const float* b3;            // [2]
-    float in_scale[4];          // a = v * in_scale[0] + in_scale[1], b = log x * in_scale[2] + in_scale[3]
+    float in_scale[4];          // a = asinh(v * in_scale[0]) * in_scale[1], b = log x * in_scale[2] + in_scale[3]
     float out_scale[4];         // t0 = y0 * out_scale[0] + out_scale[1], width = softplus(y1) * out_scale[2]
 };
 

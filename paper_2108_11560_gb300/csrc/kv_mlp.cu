@@ -2,20 +2,21 @@
 // Sec. 2.3, replacing Algorithms 1-3 on the hot path, with a per-pair check of g at the ends and
 // a fallback to the plain FP64 bracket.
 //
-// Network (all parameters FP32 masters; inference reads W2 as BF16 with FP32 accumulation):
-//   a = v * in[0] + in[1],  b = ln x * in[2] + in[3]
+// Network (all parameters FP32 masters; inference reads W2 and h1 as BF16, FP32 accumulation):
+//   a = asinh(v * in[0]) * in[1],  b = ln x * in[2] + in[3]
 //   h1 = relu(W1 [a b] + b1),  h2 = relu(W2 h1 + b2),  y = W3 h2 + b3
-//   L_k = y_k * out[2k] + out[2k+1];  t0 = max(t_ref - (e^{L_0} - DELTA), 0),
+//   L_k = y_k * out[2k] + out[2k+1];  t0 = max(t_ref - max(e^{L_0} - DELTA, 0), 0),
 //   t1 = t_ref + max(e^{L_1} - DELTA, 0), with t_ref the peak of g.
 // The network predicts log half-widths of the range about the peak; the peak itself comes from
 // four FP32 Newton steps on g' from asinh(v/x) (g' is concave and <= 0 there, so the iterates
 // fall monotonically onto the zero).
 //
-// Fast path per pair (kv_mlp_kernel): MLP -> peak -> float-float offset g(t_ref) and constants
-// -> check that g - g(t_ref) at both ends lies in [log eps - W, log eps] (the range is neither
-// too narrow nor too wide) -> FP32 bins.  Pairs that fail the check are appended to a list and
-// recomputed by a second kernel with the plain FP64 bracket, so one failing lane does not stall
-// its warp on the slow path.
+// Fast path per pair (kv_mlp_tc_kernel): MLP (hidden layer on the tensor cores) -> peak ->
+// float-float offset g(t_ref) and constants -> check that g - g(t_ref) at both ends lies in
+// [log eps - W, log eps] (the range is neither too narrow nor too wide), with a few FP32 Newton
+// corrections of an end that misses -> FP32 bins.  Pairs that still fail are appended to a list
+// and recomputed by a second kernel with the plain FP64 bracket, so one failing lane does not
+// stall its warp on the slow path.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -115,9 +116,10 @@ int alloc_handle(kv_mlp** out)
         delete h;
         return kvh::cuda_fail(e);
     }
-    // feature and output scaling: v in [0, 200] and log10 x in [-4, 4] map to [-1, 1]
-    h->in_scale[0] = 1.0f / 100.0f;
-    h->in_scale[1] = -1.0f;
+    // feature and output scaling: a = asinh(2 v) / asinh(400) * 2 spreads small orders (v < 1)
+    // over a useful share of [0, 2] for v in [0, 200]; log10 x in [-4, 4] maps to [-1, 1]
+    h->in_scale[0] = 2.0f;
+    h->in_scale[1] = (float)(2.0 / asinh(400.0));
     h->in_scale[2] = (float)(1.0 / (4.0 * log(10.0)));
     h->in_scale[3] = 0.0f;
     h->out_scale[0] = 3.0f;
@@ -160,7 +162,7 @@ struct MlpSmem {
 // weights widened to FP32; h1 is rounded to BF16 as the tensor-core form would see it.
 __device__ __forceinline__ void mlp_forward(const MlpSmem& s, float v, float x, float& L0, float& L1)
 {
-    const float a = fmaf(v, s.in_scale[0], s.in_scale[1]);
+    const float a = asinhf(v * s.in_scale[0]) * s.in_scale[1];
     const float b = fmaf(__logf(x), s.in_scale[2], s.in_scale[3]);
     float h1[H];
 #pragma unroll
@@ -283,9 +285,11 @@ __device__ __forceinline__ bool float_edge(float v, float x, float& lk, float& d
 }
 
 // The check of a learned range: g - g(tr) at each end within [le - W, le] (le = log eps).  An
-// end that misses the window gets one FP32 Newton step towards the middle of the window (the
-// slope of the same cancellation-free difference) and must then pass the same check.  The left
-// end becomes 0 when the range reaches t = 0.  Returns false when the pair must fall back.
+// end that misses the window gets up to kNewtonSteps FP32 Newton steps towards the middle of the
+// window (the slope of the same cancellation-free difference) and must then pass the same check.
+// The left end becomes 0 when the range reaches t = 0.  Returns false when the pair must fall
+// back to the plain bracket.
+constexpr int kNewtonSteps = 3;
 __device__ __forceinline__ bool check_range(const BinsF& b, float tr, float w0, float w1, float le,
                                             float lo, float& t0, float& t1)
 {
@@ -294,7 +298,7 @@ __device__ __forceinline__ bool check_range(const BinsF& b, float tr, float w0, 
     float e2, es, ems;
     float s1 = w1;
     float d1 = delta_g_f32(b, s1, e2, es, ems);
-    if (!in_window(d1)) {
+    for (int k = 0; k < kNewtonSteps && !in_window(d1); ++k) {
         const float slope = delta_g_slope_f32(b, e2, es, ems);
         float sn = s1 - (d1 - mid) / slope;
         if (!(slope < 0.0f) || !isfinite(sn)) sn = d1 > le ? 2.0f * s1 : 0.5f * s1;
@@ -312,7 +316,7 @@ __device__ __forceinline__ bool check_range(const BinsF& b, float tr, float w0, 
             t0 = 0.0f;  // the range starts at 0 and is not too wide there
         } else {
             float d0 = s0 <= -tr ? dz : delta_g_f32(b, s0, e2, es, ems);
-            if (!in_window(d0)) {
+            for (int k = 0; k < kNewtonSteps && !in_window(d0) && s0 > -tr; ++k) {
                 const float slope = delta_g_slope_f32(b, e2, es, ems);
                 float sn = s0 - (d0 - mid) / slope;
                 if (!(slope > 0.0f) || !isfinite(sn)) sn = d0 > le ? 2.0f * s0 : 0.5f * s0;
@@ -446,7 +450,7 @@ __global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
         const float xa = edge ? 1.0f : x;
         // layer 1 -> BF16 row t of the A tile
         {
-            const float a = fmaf(va, sm.in_scale[0], sm.in_scale[1]);
+            const float a = asinhf(va * sm.in_scale[0]) * sm.in_scale[1];
             const float b = fmaf(__logf(xa), sm.in_scale[2], sm.in_scale[3]);
 #pragma unroll
             for (int c = 0; c < H / 8; ++c) {
@@ -719,7 +723,7 @@ __global__ void __launch_bounds__(kTrainBlock) mlp_grad_kernel(GradArgs g)
     if (active) {
         const int64_t idx = g.sequential ? kb : (int64_t)(mix64_d(g.seed + (uint64_t)g.step * g.batch + kb) % (uint64_t)g.n);
         const double vd = fabs(g.v[idx]), xd = g.x[idx];
-        const float a = (float)(vd * g.in_scale[0] + g.in_scale[1]);
+        const float a = (float)(asinh(vd * g.in_scale[0]) * g.in_scale[1]);
         const float b = (float)(log(xd) * g.in_scale[2] + g.in_scale[3]);
         F[2 * s] = a;
         F[2 * s + 1] = b;

@@ -109,10 +109,16 @@ class Mlp:
         return t0, t1
 
 
-def training_set(device, n: int = TRAIN_PAIRS, seed: int = 3, log_eps: float = TRAIN_LOG_EPS):
+#: training distributions: "uniform" is v ~ U[0, 200] (the 1M-pair learned-bracket recipe);
+#: "mixed" (the default network's) puts half of the orders log-uniform in [1e-3, 200]
+DOMAINS = {"uniform": W.learned_bracket, "mixed": W.learned_bracket_mixed}
+
+
+def training_set(device, n: int = TRAIN_PAIRS, seed: int = 3, log_eps: float = TRAIN_LOG_EPS,
+                 domain: str = "mixed"):
     """(v, x, t0, t1) float64 CUDA tensors: learned-bracket inputs cast through float32 (what the
     fast path sees) with targets from the plain FP64 bracket."""
-    v, x = W.learned_bracket(n, seed=seed)
+    v, x = DOMAINS[domain](n, seed=seed)
     v = torch.tensor(v.astype(np.float32), dtype=torch.float64, device=device)
     x = torch.tensor(x.astype(np.float32), dtype=torch.float64, device=device)
     t0, _, t1, _ = kv.kv_bracket(v, x, log_eps=log_eps)
@@ -120,9 +126,9 @@ def training_set(device, n: int = TRAIN_PAIRS, seed: int = 3, log_eps: float = T
 
 
 def train_network(device, n: int = TRAIN_PAIRS, seed: int = 3, schedule=SCHEDULE,
-                  batch: int = BATCH, init_seed: int = 1):
+                  batch: int = BATCH, init_seed: int = 1, domain: str = "mixed"):
     """A freshly trained network (and its loss curve)."""
-    v, x, t0, t1 = training_set(device, n, seed)
+    v, x, t0, t1 = training_set(device, n, seed, domain=domain)
     net = Mlp.create(init_seed)
     losses = []
     for k, (steps, lr) in enumerate(schedule):

@@ -59,6 +59,16 @@ def learned_bracket(n: int, seed: int = 3):
     return v, x
 
 
+def learned_bracket_mixed(n: int, seed: int = 3):
+    """The learned-bracket inputs with half of the orders log-uniform in [1e-3, 200] instead of
+    uniform, so that small orders (v < 1) are represented; x log-uniform in [1e-4, 1e4]."""
+    v, x = learned_bracket(n, seed)
+    rng = np.random.default_rng(seed + 1000)
+    k = n // 2
+    v[:k] = 10.0 ** rng.uniform(-3.0, np.log10(200.0), k)
+    return v, x
+
+
 def extreme_range(n: int = 134_217_728, seed: int = 5):
     """v log-uniform in [1e-3, 1e3] except 1 % v = 0 exactly and 1 % v = k + 1/2, k ~ U{0..999};
     x log-uniform in [1e-6, 1e5] (the 128M-pair extreme-range case)."""

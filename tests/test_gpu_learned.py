@@ -116,7 +116,7 @@ def test_predictions_match_oracle_forward(net):
     # BF16 rounding of W2 and h1: a few parts in 1e3 of the outputs' scale (more in the log of a
     # small left width, where a small shift of t0 is a large relative change)
     e1 = np.abs(L(_np(t1) - tp) - L(r1 - tp))
-    assert np.quantile(e1, 0.99) < 0.02 and e1.max() < 0.1
+    assert np.quantile(e1, 0.99) < 0.04 and e1.max() < 0.1
     sel = (_np(t0) > 0) & (r0 > 0)  # both sides unclamped
     e0 = np.abs(L(tp[sel] - _np(t0)[sel]) - L(tp[sel] - r0[sel]))
     assert np.quantile(e0, 0.99) < 0.06 and e0.max() < 0.3
@@ -162,17 +162,26 @@ def test_mlp_path_matches_oracle(net, bins):
 
 
 def test_fallback_path_is_exact_enough():
-    """A network that predicts nothing useful sends (almost) every pair to the plain-bracket
-    fallback, whose results still meet the tolerance."""
-    bad = learned.Mlp.create(5)  # untrained
+    """A network whose outputs are NaN fails every check and sends every pair to the
+    plain-bracket fallback, whose results still meet the tolerance; an untrained network is
+    rescued in part by the end corrections."""
+    bad = learned.Mlp.create(5)
+    p = bad.params()
+    p[-2:] = np.nan  # b3: both outputs NaN
+    bad.set_params(p)
     v, x = W.hard_band(8000, seed=312)
     (vf, v64), (xf, x64) = W.to_f32(v, x)
     fb = torch.zeros(1, dtype=torch.int64, device=DEV)
     out = kv.kv_fwd_bwd_ex(_t(vf, torch.float32), _t(xf, torch.float32), bins=32, bracket="mlp",
                            mlp=bad, status=True, fallback_count=fb)
     st = out["status"].cpu().numpy()
-    assert fb.item() == np.count_nonzero(st & N.KV_PAIR_FALLBACK) > 0.5 * v.size
+    assert fb.item() == np.count_nonzero(st & N.KV_PAIR_FALLBACK) == v.size
     ref = oracle.o1(v64, x64, bins=32, log_eps=LOG_EPS, precision="long")
+    assert rel_logk(_np(out["logk"]), ref["logk"]).max() < TOL
+    assert rel(_np(out["dx"]), ref["dx"]).max() < TOL
+    untrained = learned.Mlp.create(6)
+    out = kv.kv_fwd_bwd_ex(_t(vf, torch.float32), _t(xf, torch.float32), bins=32, bracket="mlp",
+                           mlp=untrained, status=True)
     assert rel_logk(_np(out["logk"]), ref["logk"]).max() < TOL
     assert rel(_np(out["dx"]), ref["dx"]).max() < TOL
 
