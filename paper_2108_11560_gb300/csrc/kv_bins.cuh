@@ -114,36 +114,36 @@ struct BinsF {
 // phi(s) = e^s - 1 - s and phi(-s), and e^{+-s}, each to a few FP32 ulps relative.
 // |s| <= 2: even/odd Taylor parts of phi in z = s^2 (terms to s^15; the rest < 2e-9 relative).
 // |s| > 2: from expf (no cancellation there: phi(2) = 4.39, phi(-2) = 1.14).
+// Both forms are computed (the series on s clamped to [-2, 2]) and the valid one is selected:
+// lanes of a warp whose bins straddle |s| = 2 would otherwise run both sides one after the other.
 __device__ __forceinline__ void phi_pair(float s, float& php, float& phm, float& es, float& ems)
 {
-    if (fabsf(s) <= 2.0f) {
-        float z = s * s;
-        // E(z) = sum_{k>=1} z^{k-1}/(2k)!,  O(z) = sum_{k>=1} z^{k-1}/(2k+1)!
-        float E = 1.0f / 87178291200.0f;  // 1/14!
-        E = fmaf(E, z, 1.0f / 479001600.0f);
-        E = fmaf(E, z, 1.0f / 3628800.0f);
-        E = fmaf(E, z, 1.0f / 40320.0f);
-        E = fmaf(E, z, 1.0f / 720.0f);
-        E = fmaf(E, z, 1.0f / 24.0f);
-        E = fmaf(E, z, 0.5f);
-        float O = 1.0f / 1307674368000.0f;  // 1/15!
-        O = fmaf(O, z, 1.0f / 6227020800.0f);
-        O = fmaf(O, z, 1.0f / 39916800.0f);
-        O = fmaf(O, z, 1.0f / 362880.0f);
-        O = fmaf(O, z, 1.0f / 5040.0f);
-        O = fmaf(O, z, 1.0f / 120.0f);
-        O = fmaf(O, z, 1.0f / 6.0f);
-        float so = s * O;
-        php = z * (E + so);
-        phm = z * (E - so);
-        es = (1.0f + s) + php;
-        ems = (1.0f - s) + phm;
-    } else {
-        es = expf(s);
-        ems = expf(-s);
-        php = (es - 1.0f) - s;
-        phm = (ems - 1.0f) + s;
-    }
+    const float sc = fminf(fmaxf(s, -2.0f), 2.0f);
+    const float z = sc * sc;
+    // E(z) = sum_{k>=1} z^{k-1}/(2k)!,  O(z) = sum_{k>=1} z^{k-1}/(2k+1)!
+    float E = 1.0f / 87178291200.0f;  // 1/14!
+    E = fmaf(E, z, 1.0f / 479001600.0f);
+    E = fmaf(E, z, 1.0f / 3628800.0f);
+    E = fmaf(E, z, 1.0f / 40320.0f);
+    E = fmaf(E, z, 1.0f / 720.0f);
+    E = fmaf(E, z, 1.0f / 24.0f);
+    E = fmaf(E, z, 0.5f);
+    float O = 1.0f / 1307674368000.0f;  // 1/15!
+    O = fmaf(O, z, 1.0f / 6227020800.0f);
+    O = fmaf(O, z, 1.0f / 39916800.0f);
+    O = fmaf(O, z, 1.0f / 362880.0f);
+    O = fmaf(O, z, 1.0f / 5040.0f);
+    O = fmaf(O, z, 1.0f / 120.0f);
+    O = fmaf(O, z, 1.0f / 6.0f);
+    const float so = sc * O;
+    const float pp = z * (E + so), pm = z * (E - so);
+    const float eb = expf(s);
+    const float ebi = rcp_approx(eb);
+    const bool small = fabsf(s) <= 2.0f;
+    php = small ? pp : (eb - 1.0f) - s;
+    phm = small ? pm : (ebi - 1.0f) + s;
+    es = small ? (1.0f + sc) + pp : eb;
+    ems = small ? (1.0f - sc) + pm : ebi;
 }
 
 // tanh(y) for |y| < 0.625 by its Taylor series through y^19 (relative error < 1e-8 there);

@@ -335,32 +335,6 @@ __device__ __forceinline__ bool check_range(const BinsF& b, float tr, float w0, 
     return ok;
 }
 
-// Bins, epilogue and stores of a pair whose range passed the check.
-template <bool DERIV>
-__device__ __forceinline__ void finish_pair(const MlpPathParams& p, int64_t i, float v, PeakConst& c,
-                                            float t0, float t1)
-{
-    c.b.s0 = t0 - c.b.tp;
-    c.b.h = (t1 - t0) / (float)p.bins;
-    c.b.n = p.bins;
-    float S0, S1, S2;
-    sums_f32<1, DERIV>(c.b, 0, S0, S1, S2);
-    df L = df_add(c.G, df_make(logf(c.b.h * S0)));
-    const float lk = L.hi + L.lo;
-    const float r = 1.0f / S0;
-    float dv = DERIV ? copysignf(S1 * r, v) : 0.0f;
-    if (v == 0.0f) dv = 0.0f;
-    float dx = DERIV ? -(S2 * r) : 0.0f;
-    if (p.go) {
-        dv *= p.go[i];
-        dx *= p.go[i];
-    }
-    if (p.logk) p.logk[i] = lk;
-    if (p.dv) p.dv[i] = dv;
-    if (p.dx) p.dx[i] = dx;
-    if (p.status) p.status[i] = KV_PAIR_OK;
-}
-
 // ------------------------------------------------------------------ tensor-core hidden layer
 
 // Shared-memory matrix descriptor of the tcgen05 MMA for a K-major tile without swizzling:
@@ -516,8 +490,42 @@ __global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
-        if (!active) continue;
-        if (edge) {
+        // Every lane runs the same straight-line code from here (edge and inactive lanes on
+        // their placeholder inputs), so the warp is converged when it enters the bins:
+        // otherwise lanes that took a different path through the check would run the bins
+        // separately, once per group.
+        const float L0 = fmaf(y0, sm.out_scale[0], sm.out_scale[1]);
+        const float L1 = fmaf(y1, sm.out_scale[2], sm.out_scale[3]);
+        const float tr = peak_f32(va, xa);
+        const float w0 = fmaxf(__expf(L0) - DELTA, 0.0f);
+        const float w1 = fmaxf(__expf(L1) - DELTA, 1e-6f * (1.0f + tr));
+        float t0, t1;
+        PeakConst c = peak_constants(va, xa, tr);
+        const bool ok = check_range(c.b, tr, w0, w1, p.log_eps, lo_ok, t0, t1);
+        const bool regular = active && !edge;
+        if (regular && !ok) {
+            uint32_t k = atomicAdd(p.fb_count, 1u);
+            p.fb_list[k] = (uint32_t)i;
+        }
+        if (!ok) {  // keep the bins of a failed lane finite; its results are not stored
+            t0 = fmaxf(tr - 1.0f, 0.0f);
+            t1 = tr + 1.0f;
+        }
+        __syncwarp();
+        c.b.s0 = t0 - c.b.tp;
+        c.b.h = (t1 - t0) / (float)p.bins;
+        c.b.n = p.bins;
+        float S0, S1, S2;
+        sums_f32<1, DERIV>(c.b, 0, S0, S1, S2);
+        if (regular && ok) {
+            df L = df_add(c.G, df_make(logf(c.b.h * S0)));
+            lk = L.hi + L.lo;
+            const float r = 1.0f / S0;
+            dv = DERIV ? copysignf(S1 * r, v) : 0.0f;
+            if (v == 0.0f) dv = 0.0f;
+            dx = DERIV ? -(S2 * r) : 0.0f;
+        }
+        if (active && (edge || ok)) {
             if (p.go) {
                 dv *= p.go[i];
                 dx *= p.go[i];
@@ -525,22 +533,8 @@ __global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
             if (p.logk) p.logk[i] = lk;
             if (p.dv) p.dv[i] = dv;
             if (p.dx) p.dx[i] = dx;
-            if (p.status) p.status[i] = KV_PAIR_EDGE;
-            continue;
+            if (p.status) p.status[i] = edge ? KV_PAIR_EDGE : KV_PAIR_OK;
         }
-        const float L0 = fmaf(y0, sm.out_scale[0], sm.out_scale[1]);
-        const float L1 = fmaf(y1, sm.out_scale[2], sm.out_scale[3]);
-        const float tr = peak_f32(va, x);
-        const float w0 = fmaxf(__expf(L0) - DELTA, 0.0f);
-        const float w1 = fmaxf(__expf(L1) - DELTA, 1e-6f * (1.0f + tr));
-        float t0, t1;
-        PeakConst c = peak_constants(va, x, tr);
-        if (!check_range(c.b, tr, w0, w1, p.log_eps, lo_ok, t0, t1)) {
-            uint32_t k = atomicAdd(p.fb_count, 1u);
-            p.fb_list[k] = (uint32_t)i;
-            continue;
-        }
-        finish_pair<DERIV>(p, i, v, c, t0, t1);
     }
     if (aborted) {
         // a tensor-core wait ran out: the remaining pairs of this CTA go to the fallback pass

@@ -111,7 +111,8 @@ class Mlp:
 
 #: training distributions: "uniform" is v ~ U[0, 200] (the 1M-pair learned-bracket recipe);
 #: "mixed" (the default network's) puts half of the orders log-uniform in [1e-3, 200]
-DOMAINS = {"uniform": W.learned_bracket, "mixed": W.learned_bracket_mixed}
+DOMAINS = {"uniform": W.learned_bracket, "mixed": W.learned_bracket_mixed,
+           "extreme": W.extreme_training}
 
 
 def training_set(device, n: int = TRAIN_PAIRS, seed: int = 3, log_eps: float = TRAIN_LOG_EPS,

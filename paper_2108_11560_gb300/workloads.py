@@ -82,6 +82,16 @@ def extreme_range(n: int = 134_217_728, seed: int = 5):
     return v, x
 
 
+def extreme_training(n: int, seed: int = 4):
+    """Training inputs for a network covering the extreme range: half of the orders log-uniform
+    in [1e-3, 1e3], half uniform in [0, 1000]; x log-uniform in [1e-6, 1e5]."""
+    rng = np.random.default_rng(seed)
+    k = n // 2
+    v = np.concatenate([10.0 ** rng.uniform(-3.0, 3.0, k), rng.uniform(0.0, 1000.0, n - k)])
+    x = 10.0 ** rng.uniform(-6.0, 5.0, n)
+    return v, x
+
+
 def full_domain(n: int, seed: int = 7):
     """v ~ U[0, 1000], x log-uniform in [1e-6, 1e5] (the accuracy targets' whole domain)."""
     rng = np.random.default_rng(seed)

@@ -1,0 +1,139 @@
+"""The remaining workload configurations on the GPU, each checked against the oracle on sampled
+pairs (the full outputs are far too many for the CPU): the learned-bracket evaluation (64M fresh
+pairs, network trained on 1M uniform-order brackets), the extreme range (128M pairs, 64 and 256
+bins, learned-bracket mixed path against the plain FP64 path) and the paper's vectorised-timing
+inputs (Sec. 3.4).  Throughputs and fallback rates are printed (pytest -s) for the record."""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle
+from conftest import rel, rel_logk
+from paper_2108_11560_gb300 import _native as N
+from paper_2108_11560_gb300 import kv, learned
+from paper_2108_11560_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0)
+TOL_MIXED = 2e-6
+TOL_F64 = 1e-13
+LOG_EPS = -20.0
+
+
+def _timed(fn, reps=3):
+    fn()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t) / reps
+
+
+def _check_sample(out, v64, x64, idx, bins, tol=TOL_MIXED, truth=False):
+    ref = oracle.o1(v64[idx], x64[idx], bins=bins, log_eps=LOG_EPS, precision="long")
+    lk = out["logk"].cpu().numpy().astype(np.float64)[idx]
+    dv = out["dv"].cpu().numpy().astype(np.float64)[idx]
+    dx = out["dx"].cpu().numpy().astype(np.float64)[idx]
+    assert rel_logk(lk, ref["logk"]).max() < tol
+    z = v64[idx] == 0
+    assert np.all(dv[z] == 0)
+    assert rel(dv[~z], ref["dv"][~z]).max() < tol
+    assert rel(dx, ref["dx"]).max() < tol
+    if truth:
+        k = idx[:1024]
+        d = oracle.dense(v64[k], x64[k])
+        assert rel_logk(lk[:1024], d["logk"]).max() < tol
+        assert rel(dx[:1024], d["dx"]).max() < tol
+
+
+def test_learned_bracket_eval_64M():
+    """Network trained on 1M plain brackets over v in [0, 200] (uniform), x log-uniform in
+    [1e-4, 1e4]; 64M fresh pairs of the same distribution: fallback rate, accuracy, speed."""
+    net, _ = learned.train_network(DEV, domain="uniform")
+    n = 64 * 1024 * 1024
+    v, x = W.learned_bracket(n, seed=6)
+    vf, xf = v.astype(np.float32), x.astype(np.float32)
+    del v, x
+    vt, xt = torch.from_numpy(vf).to(DEV), torch.from_numpy(xf).to(DEV)
+    fb = torch.zeros(1, dtype=torch.int64, device=DEV)
+    out = kv.kv_fwd_bwd_ex(vt, xt, bins=40, bracket="mlp", mlp=net, fallback_count=fb)
+    torch.cuda.synchronize()
+    rate = fb.item() / n
+    t_mlp = _timed(lambda: kv.kv_fwd_bwd_ex(vt, xt, bins=40, bracket="mlp", mlp=net, out=out))
+    sub = slice(0, 1 << 22)
+    t_plain = _timed(lambda: kv.kv_fwd_bwd_ex(vt[sub], xt[sub], bins=40), reps=1) * (n / (1 << 22))
+    print(f"\n[learned-bracket eval 64M] fallback rate {rate:.2e}; learned {n / t_mlp:.3e} pairs/s, "
+          f"plain FP64 bracket {n / t_plain:.3e} pairs/s")
+    assert rate < 2e-3
+    idx = np.random.default_rng(401).choice(n, 4096, replace=False)
+    _check_sample(out, vf.astype(np.float64), xf.astype(np.float64), idx, 40, truth=True)
+
+
+@pytest.mark.parametrize("bins", [64, 256])
+def test_extreme_range_128M(bins):
+    """128M pairs, v log-uniform in [1e-3, 1e3] with 1 % v = 0 and 1 % half-integers, x
+    log-uniform in [1e-6, 1e5]: learned-bracket mixed path (network trained on this range) against
+    the plain FP64 path, both against the oracle."""
+    net = _extreme_network()
+    n = 128 * 1024 * 1024
+    v, x = W.extreme_range(n, seed=5)
+    vf, xf = v.astype(np.float32), x.astype(np.float32)
+    del v, x
+    vt, xt = torch.from_numpy(vf).to(DEV), torch.from_numpy(xf).to(DEV)
+    fb = torch.zeros(1, dtype=torch.int64, device=DEV)
+    out = kv.kv_fwd_bwd_ex(vt, xt, bins=bins, bracket="mlp", mlp=net, fallback_count=fb)
+    torch.cuda.synchronize()
+    rate = fb.item() / n
+    t_mlp = _timed(lambda: kv.kv_fwd_bwd_ex(vt, xt, bins=bins, bracket="mlp", mlp=net, out=out), reps=1)
+    v64, x64 = vf.astype(np.float64), xf.astype(np.float64)
+    idx = np.random.default_rng(402 + bins).choice(n, 4096, replace=False)
+    _check_sample(out, v64, x64, idx, bins, truth=True)
+    # the plain FP64 path on a 2M slice (the same pairs in double)
+    m = 1 << 21
+    v64t, x64t = torch.from_numpy(v64[:m]).to(DEV), torch.from_numpy(x64[:m]).to(DEV)
+    o64 = kv.kv_fwd_bwd_ex(v64t, x64t, bins=bins)
+    t64 = _timed(lambda: kv.kv_fwd_bwd_ex(v64t, x64t, bins=bins, out=o64), reps=1)
+    k = np.random.default_rng(403).choice(m, 1024, replace=False)
+    ref = oracle.o1(v64[k], x64[k], bins=bins, precision="long")
+    assert rel_logk(o64["logk"].cpu().numpy()[k], ref["logk"]).max() < TOL_F64
+    assert rel(o64["dx"].cpu().numpy()[k], ref["dx"]).max() < TOL_F64
+    print(f"\n[extreme 128M, {bins} bins] fallback rate {rate:.2e}; learned mixed {n / t_mlp:.3e} "
+          f"pairs/s; plain FP64 {m / t64:.3e} pairs/s")
+    assert n / t_mlp > 5 * (m / t64)
+
+
+_EXTREME = {}
+
+
+def _extreme_network():
+    if "net" not in _EXTREME:
+        _EXTREME["net"], _ = learned.train_network(DEV, domain="extreme", seed=4)
+    return _EXTREME["net"]
+
+
+def test_paper_scaling_inputs():
+    """The paper's vectorised-timing inputs (Sec. 3.4: v = 10^{2r} - 1, x = 10^{3r - 1}) at
+    array sizes 10 ... 10^7: results against the oracle, and time per call (flat while the GPU
+    is not full, then linear)."""
+    net = learned.default_network(DEV)
+    times = {}
+    for e in range(1, 8):
+        n = 10 ** e
+        v, x = W.paper_scaling(n, seed=8)
+        vt = torch.tensor(v, dtype=torch.float32, device=DEV)
+        xt = torch.tensor(x, dtype=torch.float32, device=DEV)
+        out = kv.kv_fwd_bwd_ex(vt, xt, bracket="mlp", mlp=net)
+        times[n] = _timed(lambda: kv.kv_fwd_bwd_ex(vt, xt, bracket="mlp", mlp=net, out=out))
+        if n <= 10 ** 4:
+            v64 = vt.double().cpu().numpy()
+            x64 = xt.double().cpu().numpy()
+            _check_sample(out, v64, x64, np.arange(n), 40)
+    print("\n[paper scaling inputs] " + ", ".join(f"N={n}: {1e3 * t:.3f} ms" for n, t in times.items()))
+    assert times[10 ** 4] < 5 * times[10]  # flat while the GPU is not full (Sec. 3.4's property)
