@@ -37,10 +37,21 @@ N_PAIRS = 16_777_216
 WORKLOAD = "hard_band_16M"
 MIXED_LOG_EPS = -20.0
 
-# Algorithmic FP32 work of one bin of the mixed path (the formula of the FP32 bin sum, counted
-# operation by operation with an FMA as one operation; see the design notes) and its MUFU work.
-FP32_OPS_PER_BIN = 58
-MUFU_OPS_PER_BIN = 4
+# Algorithmic FP32 work of the learned-bracket fast path, counted operation by operation from
+# its formulas with an FMA as one operation (derivation in the design notes):
+#   per bin: phi(+-s) 29, the difference g - g(t_p) and its weight 10, three compensated sums 12,
+#            the two derivative integrands 9, the bin's abscissa 1          -> 61 (+ 6 MUFU)
+#   per pair: features and layer 1 ~150, layer 3 192, peak Newton ~155, float-float offset and
+#             constants ~430, endpoint check ~115, setup and epilogue ~30     -> 1070
+# (the 64x64 hidden layer runs on the tensor cores and is not counted here).  ncu's executed
+# FFMA + FADD + FMUL counters agree: 61.2 per bin and 1069 per pair (4M pairs at 1 and 32 bins).
+FP32_OPS_PER_BIN = 61
+MUFU_OPS_PER_BIN = 6
+FP32_OPS_PER_PAIR = 1070
+# DRAM bytes per pair of the fast-path kernel, from one ncu capture (50.49 MB read + 8.80 MB
+# written for 4,194,304 pairs; profiles/kv_mlp_tc_kernel_hard_band_4M.md), scaled to a launch.
+# Set to None whenever the kernel changes until it is captured again.
+TRAFFIC_BYTES_PER_PAIR = (50.489088e6 + 8.795136e6) / 4194304
 
 
 def _env_rank():
@@ -277,13 +288,22 @@ def main():
     # FP32 pipe: 128 lanes per SM per clock (an FMA counted as one operation), at the max SM clock
     peak_ops = sms * 128 * sm_mhz * 1e6
     launch_ms = total_ms / args.steps
-    ops = n_pairs * (args.bins + 1) * FP32_OPS_PER_BIN
+    # the step's two launches: the fast-path kernel is > 99.8 % of the GPU time (launch list in
+    # profiles/launches_bench_hard_band_16M.md), so its launch time is taken as the step time
+    if args.bracket == "mlp":
+        ops = n_pairs * (FP32_OPS_PER_PAIR + (args.bins + 1) * FP32_OPS_PER_BIN)
+        traffic = (n_pairs * TRAFFIC_BYTES_PER_PAIR) if TRAFFIC_BYTES_PER_PAIR else None
+        kernel = "kv_mlp_tc_kernel"
+    else:  # the plain path is bound by the FP64 bracket; only its FP32 bins are counted
+        ops = n_pairs * (args.bins + 1) * FP32_OPS_PER_BIN
+        traffic = None
+        kernel = "kv_mixed_kernel"
     achieved = ops / (launch_ms / 1e3)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                 "unit": "Tops/s (FP32 pipe, FMA = 1 op)", "frac": achieved / peak_ops,
-                "traffic": None, "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz "
-                                                   f"({peak_src} max clock)",
-                "kernel": "kv_mixed_kernel" if args.bracket == "plain" else "kv_mlp_kernel"}
+                "traffic": traffic, "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz "
+                                                      f"({peak_src} max clock)",
+                "kernel": kernel}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
