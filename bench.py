@@ -54,9 +54,7 @@ FP32_OPS_PER_PAIR = 1070
 TRAFFIC_BYTES_PER_PAIR = (50.489088e6 + 8.795136e6) / 4194304
 
 
-def _env_rank():
-    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(
-        os.environ.get("WORLD_SIZE", "1"))
+from paper_2108_11560_gb300.distributed import all_reduce_scalar, env_rank as _env_rank  # noqa: E402
 
 
 def _peaks():
@@ -191,9 +189,7 @@ def end_to_end(args, vf, xf, mlp, dist, dev, world):
         kv.kv_fwd_bwd_host(hv, hx, bins=args.bins, bracket=args.bracket, mlp=mlp, out=hout)
     secs = time.perf_counter() - t0
     if dist:
-        t = torch.tensor([secs], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs = float(t.item())
+        secs = all_reduce_scalar(secs, "max", device=dev)
     return {"value": world * n * steps / secs, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * n,
             "d2h_bytes_per_step": 3 * 4 * n}
 
@@ -268,9 +264,7 @@ def main():
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = all_reduce_scalar(total_ms, "max", device=dev)
     value = world * n_pairs * args.steps / (total_ms / 1e3)
 
     # end to end: the same call on pinned host buffers, copies inside the timed region

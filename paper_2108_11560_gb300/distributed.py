@@ -1,0 +1,47 @@
+"""Host-side helpers for one process per GPU.
+
+The pairs (v, x) are independent, so the path shards without any exchange: each rank takes a
+contiguous share of the arrays and computes it alone.  The only collectives are scalar ones
+outside the data path: the sum of a sharded log-likelihood sum_i log K(v_i, x_i) and the
+maximum of per-rank timings.  These helpers work with any torch.distributed backend (NCCL on
+GPUs, gloo in the CPU tests).
+"""
+from __future__ import annotations
+
+import os
+
+
+def env_rank():
+    """(rank, local_rank, world_size) from the torchrun environment (0, 0, 1 when absent)."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def shard_bounds(n: int, rank: int, world: int):
+    """Contiguous share [lo, hi) of n items for one rank; shares differ in size by at most one
+    and cover [0, n) exactly once."""
+    if world < 1 or not (0 <= rank < world) or n < 0:
+        raise ValueError("need world >= 1, 0 <= rank < world and n >= 0")
+    base, extra = divmod(n, world)
+    lo = rank * base + min(rank, extra)
+    hi = lo + base + (1 if rank < extra else 0)
+    return lo, hi
+
+
+def all_reduce_scalar(value: float, op: str = "sum", device=None) -> float:
+    """Sum or maximum of one float over all ranks (the value itself without a process group)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op={"sum": dist.ReduceOp.SUM, "max": dist.ReduceOp.MAX}[op])
+    return float(t.item())
+
+
+def sharded_loglik(v, x, rank: int, world: int, local_sum, device=None) -> float:
+    """sum_i log K(v_i, x_i) over all ranks: each rank passes its share of the full arrays to
+    `local_sum` (on a GPU: kv.kv_sum of kv.kv_log) and the partial sums meet in one all-reduce."""
+    lo, hi = shard_bounds(len(v), rank, world)
+    return all_reduce_scalar(float(local_sum(v[lo:hi], x[lo:hi])), "sum", device)
