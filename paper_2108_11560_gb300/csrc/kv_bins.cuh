@@ -14,7 +14,8 @@
 // so that in FP32 every term is small where the weight is large and no two large terms cancel:
 //   g(t) - g(t_p) = (v - x sinh t_p) s + [log1p(e^{-2vt}) - log1p(e^{-2u})]
 //                   - (x e^{t_p}/2) phi(s) - (x e^{-t_p}/2) phi(-s).
-// The per-pair constants (v - x sinh t_p, x e^{+-t_p}/2, log1p(e^{-2u}), g(t_p)) are FP64.
+// The per-pair constants (v - x sinh t_p, x e^{+-t_p}/2, log1p(e^{-2u}), g(t_p)) carry extra
+// precision: FP64 with the plain bracket, float-float with the learned one.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -163,20 +164,22 @@ __device__ __forceinline__ float tanh_small(float y)
     return fmaf(y * z, p, y);
 }
 
-// g(t_p + s) - g(t_p) in FP32 by the cancellation-free form above (the FP32 bin formula), with
-// e^{-2vt} and e^{+-s} returned for the derivative integrands.
-__device__ __forceinline__ float delta_g_f32(const BinsF& b, float s, float& e2, float& es,
-                                             float& ems)
+// g(t_p + s) - g(t_p) to about 1e-3 in absolute terms, for the range check (whose window is 12
+// wide): the same form with e^{+-s} from ex2.approx and phi(+-s) = e^{+-s} - 1 -+ s directly
+// (no series), with e^{-2vt} and e^{+-s} returned for the slope.
+__device__ __forceinline__ float delta_g_coarse(const BinsF& b, float s, float& e2, float& es,
+                                                float& ems)
 {
-    float php, phm;
-    phi_pair(s, php, phm, es, ems);
-    float vt = fmaf(b.v, s, b.u);
+    es = ex2_approx(s * LOG2E_F);
+    ems = rcp_approx(es);
+    const float vt = fmaf(b.v, s, b.u);
     e2 = ex2_approx(-2.0f * LOG2E_F * vt);
-    float d = fmaf(lg2_approx(1.0f + e2), LN2_F, -b.lu);
+    const float d = fmaf(lg2_approx(1.0f + e2), LN2_F, -b.lu);
+    const float php = (es - 1.0f) - s, phm = (ems - 1.0f) + s;
     return fmaf(b.c1, s, d) - fmaf(b.ap, php, b.am * phm);
 }
 
-// d/ds of delta_g_f32 at the same s, from the values it returned: g'(t_p + s) written as
+// d/ds of delta_g_coarse at the same s, from the values it returned: g'(t_p + s) written as
 // (v - x sinh t_p) - 2v e^{-2vt} / (1 + e^{-2vt}) - (x e^{t_p}/2)(e^s - 1) + (x e^{-t_p}/2)(e^{-s} - 1).
 __device__ __forceinline__ float delta_g_slope_f32(const BinsF& b, float e2, float es, float ems)
 {
@@ -184,6 +187,31 @@ __device__ __forceinline__ float delta_g_slope_f32(const BinsF& b, float e2, flo
     return b.c1 + dl - b.ap * (es - 1.0f) + b.am * (ems - 1.0f);
 }
 
+// One FP32 bin: its weight c_m e^{g(t_m) - g(t_p)} and the two derivative integrands' weights.
+template <bool DERIV>
+__device__ __forceinline__ void bin_f32(const BinsF& b, int m, float& w, float& w1, float& w2)
+{
+    const float s = fmaf((float)m, b.h, b.s0);
+    float php, phm, es, ems;
+    phi_pair(s, php, phm, es, ems);
+    const float vt = fmaf(b.v, s, b.u);
+    const float e2 = ex2_approx(-2.0f * LOG2E_F * vt);             // e^{-2vt}
+    const float d = fmaf(lg2_approx(1.0f + e2), LN2_F, -b.lu);      // log1p(e^{-2vt}) - log1p(e^{-2u})
+    const float dg = fmaf(b.c1, s, d) - fmaf(b.ap, php, b.am * phm);
+    const float c = (m == 0 || m == b.n) ? 0.5f : 1.0f;
+    w = c * ex2_approx(dg * LOG2E_F);
+    if (DERIV) {
+        const float t = b.tp + s;
+        const float th = fabsf(vt) < 0.625f ? tanh_small(vt)
+                                            : (1.0f - e2) * rcp_approx(1.0f + e2);  // tanh(vt)
+        w1 = w * (t * th);
+        w2 = w * (0.5f * fmaf(b.ep, es, b.em * ems));                 // cosh t
+    }
+}
+
+// The three sums, compensated per block of four bins: a block's four terms are added pairwise
+// (two rounding levels) and the block sum goes into a Kahan sum, so the relative error stays
+// a few units of 2^-24 for any bin count at 1.75 additions per term instead of Kahan's four.
 template <int L, bool DERIV>
 __device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, float& S1, float& S2)
 {
@@ -191,23 +219,24 @@ __device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, fl
     k0.init();
     k1.init();
     k2.init();
-    for (int m = lane; m <= b.n; m += L) {
-        float s = fmaf((float)m, b.h, b.s0);
-        float php, phm, es, ems;
-        phi_pair(s, php, phm, es, ems);
-        float vt = fmaf(b.v, s, b.u);
-        float e2 = ex2_approx(-2.0f * LOG2E_F * vt);             // e^{-2vt}
-        float d = fmaf(lg2_approx(1.0f + e2), LN2_F, -b.lu);      // log1p(e^{-2vt}) - log1p(e^{-2u})
-        float dg = fmaf(b.c1, s, d) - fmaf(b.ap, php, b.am * phm);
-        float c = (m == 0 || m == b.n) ? 0.5f : 1.0f;
-        float w = c * ex2_approx(dg * LOG2E_F);
+    int m = lane;
+    for (; m + 3 * L <= b.n; m += 4 * L) {
+        float w[4], w1[4], w2[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) bin_f32<DERIV>(b, m + q * L, w[q], w1[q], w2[q]);
+        k0.add((w[0] + w[1]) + (w[2] + w[3]));
+        if (DERIV) {
+            k1.add((w1[0] + w1[1]) + (w1[2] + w1[3]));
+            k2.add((w2[0] + w2[1]) + (w2[2] + w2[3]));
+        }
+    }
+    for (; m <= b.n; m += L) {
+        float w, w1, w2;
+        bin_f32<DERIV>(b, m, w, w1, w2);
         k0.add(w);
         if (DERIV) {
-            float t = b.tp + s;
-            float th = fabsf(vt) < 0.625f ? tanh_small(vt)
-                                          : (1.0f - e2) * rcp_approx(1.0f + e2);  // tanh(vt)
-            k1.add(w * (t * th));
-            k2.add(w * (0.5f * fmaf(b.ep, es, b.em * ems)));     // cosh t
+            k1.add(w1);
+            k2.add(w2);
         }
     }
     S0 = lane_sum<float, L>(k0.value());

@@ -132,7 +132,9 @@ int alloc_handle(kv_mlp** out)
 
 // ------------------------------------------------------------------ device pieces
 
-// The peak of g by four FP32 Newton steps from asinh(v/x) (0 when v^2 <= x).
+// The peak of g by four FP32 Newton steps from asinh(v/x) (0 when v^2 <= x).  Its accuracy does
+// not enter the results (the bins are exact relative to any reference point near the peak), so
+// the steps use the approximate exponential, reciprocal and division.
 __device__ __forceinline__ float peak_f32(float v, float x)
 {
     if (!(v * v > x)) return 0.0f;
@@ -143,11 +145,11 @@ __device__ __forceinline__ float peak_f32(float v, float x)
         float r = rcp_approx(1.0f + e2);
         float th = (1.0f - e2) * r;
         float sech2 = 4.0f * e2 * r * r;
-        float et = expf(t);
-        float eti = 1.0f / et;
+        float et = ex2_approx(t * LOG2E_F);
+        float eti = rcp_approx(et);
         float g1 = v * th - 0.5f * x * (et - eti);
         float g2 = v * v * sech2 - 0.5f * x * (et + eti);
-        float tn = t - g1 / g2;
+        float tn = t - __fdividef(g1, g2);
         if (isfinite(tn)) t = fminf(fmaxf(tn, 0.0f), t);
     }
     return t;
@@ -297,13 +299,13 @@ __device__ __forceinline__ bool check_range(const BinsF& b, float tr, float w0, 
     auto in_window = [&](float d) { return d <= le && d >= lo; };
     float e2, es, ems;
     float s1 = w1;
-    float d1 = delta_g_f32(b, s1, e2, es, ems);
+    float d1 = delta_g_coarse(b, s1, e2, es, ems);
     for (int k = 0; k < kNewtonSteps && !in_window(d1); ++k) {
         const float slope = delta_g_slope_f32(b, e2, es, ems);
         float sn = s1 - (d1 - mid) / slope;
         if (!(slope < 0.0f) || !isfinite(sn)) sn = d1 > le ? 2.0f * s1 : 0.5f * s1;
         s1 = fminf(fmaxf(sn, 0.25f * s1), 4.0f * s1);
-        d1 = delta_g_f32(b, s1, e2, es, ems);
+        d1 = delta_g_coarse(b, s1, e2, es, ems);
     }
     bool ok = in_window(d1);
     t1 = tr + s1;
@@ -311,11 +313,11 @@ __device__ __forceinline__ bool check_range(const BinsF& b, float tr, float w0, 
     if (tr > 0.0f) {
         // the left end: the predicted one, or 0 when the range reaches it
         float s0 = -fminf(w0, tr);
-        const float dz = delta_g_f32(b, -tr, e2, es, ems);  // at t = 0
+        const float dz = delta_g_coarse(b, -tr, e2, es, ems);  // at t = 0
         if (dz > le || (s0 <= -tr && dz >= lo)) {
             t0 = 0.0f;  // the range starts at 0 and is not too wide there
         } else {
-            float d0 = s0 <= -tr ? dz : delta_g_f32(b, s0, e2, es, ems);
+            float d0 = s0 <= -tr ? dz : delta_g_coarse(b, s0, e2, es, ems);
             for (int k = 0; k < kNewtonSteps && !in_window(d0) && s0 > -tr; ++k) {
                 const float slope = delta_g_slope_f32(b, e2, es, ems);
                 float sn = s0 - (d0 - mid) / slope;
@@ -325,7 +327,7 @@ __device__ __forceinline__ bool check_range(const BinsF& b, float tr, float w0, 
                     s0 = -tr;
                     d0 = dz;
                 } else {
-                    d0 = delta_g_f32(b, s0, e2, es, ems);
+                    d0 = delta_g_coarse(b, s0, e2, es, ems);
                 }
             }
             ok = ok && (in_window(d0) || (s0 <= -tr && d0 >= lo));
