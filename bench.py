@@ -39,22 +39,19 @@ MIXED_LOG_EPS = -20.0
 
 # Algorithmic FP32 work of the learned-bracket fast path, counted operation by operation from
 # its formulas with an FMA as one operation (derivation in the design notes):
-#   per bin: phi(+-s) 29, the difference g - g(t_p) and its weight 10, three compensated sums 12,
-#            the two derivative integrands 9, the bin's abscissa 1          -> 61 (+ 6 MUFU)
-#   per pair: features and layer 1 ~150, layer 3 192, peak Newton ~155, float-float offset and
-#             constants ~430, endpoint check ~115, setup and epilogue ~30     -> 1070
+#   per bin: phi(+-s) 29, the difference g - g(t_p) and its weight 10, three block-compensated
+#            sums 5.25, the two derivative integrands 9, the bin's abscissa 1   -> 55 (+ 6 MUFU)
+#   per pair: features and layer 1 ~150, layer 3 192, peak Newton ~115, float-float offset and
+#             constants ~430, endpoint check ~55, setup and epilogue ~30         -> 971
 # (the 64x64 hidden layer runs on the tensor cores and is not counted here).  ncu's executed
-# FFMA + FADD + FMUL counters agree: 61.2 per bin and 1069 per pair (4M pairs at 1 and 32 bins).
-FP32_OPS_PER_BIN = 61
+# FFMA + FADD + FMUL counters agree: 55.2 per bin and 971 per pair (4M pairs at 1 and 32 bins).
+FP32_OPS_PER_BIN = 55
 MUFU_OPS_PER_BIN = 6
-FP32_OPS_PER_PAIR = 1070
-# DRAM bytes per pair of the fast-path kernel, from one ncu capture (50.49 MB read + 8.80 MB
+FP32_OPS_PER_PAIR = 971
+# DRAM bytes per pair of the fast-path kernel, from one ncu capture (50.41 MB read + 8.96 MB
 # written for 4,194,304 pairs; profiles/kv_mlp_tc_kernel_hard_band_4M.md), scaled to a launch.
 # Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES_PER_PAIR = None  # the kernel changed after the last capture
-
-
-from paper_2108_11560_gb300.distributed import all_reduce_scalar, env_rank as _env_rank  # noqa: E402
+TRAFFIC_BYTES_PER_PAIR = (50.411520e6 + 8.958464e6) / 4194304
 
 
 def _peaks():
