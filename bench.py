@@ -30,6 +30,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2108_11560_gb300 import workloads as W  # noqa: E402
+from paper_2108_11560_gb300.distributed import all_reduce_scalar  # noqa: E402
+from paper_2108_11560_gb300.distributed import env_rank as _env_rank  # noqa: E402
 
 METRIC = "(v,x) pairs/s for log K_v(x)+∂v+∂x at ≤2e-6 rel err; % of FP32/SFU peak"
 UNIT = "pairs/s"

@@ -133,7 +133,7 @@ int kv_fwd_bwd_ex(const kv_args* a);
  * (pinned with cudaHostAlloc for full speed); every other field means what it means for
  * kv_fwd_bwd_ex, except that grad_out, status and fallback_count must be NULL.  The call copies
  * the inputs to the device, computes and copies the outputs back, pipelined in chunks of up to
- * 2^22 pairs over a->stream and an internal second stream, and returns when the host outputs
+ * 2^20 pairs rotating over a->stream and two internal streams, and returns when the host outputs
  * are complete.  Device staging memory is allocated and freed on the stream inside the call. */
 int kv_fwd_bwd_host(const kv_args* a);
 

@@ -362,14 +362,18 @@ int validate(const kv_args* a, int* bins, double* log_eps, int* max_iter, int* l
 
 extern "C" {
 
-int kv_fwd_bwd_ex(const kv_args* a)
+int kv_fwd_bwd_ex(const kv_args* a) { return kvh::fwd_bwd_ex(a, nullptr); }
+
+}  // extern "C"
+
+int kvh::fwd_bwd_ex(const kv_args* a, uint32_t* scratch)
 {
     int bins, max_iter, lanes;
     double log_eps;
     int rc = validate(a, &bins, &log_eps, &max_iter, &lanes);
     if (rc != KV_OK) return rc;
     if (a->n == 0) return KV_OK;
-    if (a->bracket == KV_BRACKET_MLP) return kvh::launch_mlp_path(a, bins, log_eps, max_iter);
+    if (a->bracket == KV_BRACKET_MLP) return kvh::launch_mlp_path(a, bins, log_eps, max_iter, scratch);
     KParams p;
     p.v = a->v;
     p.x = a->x;
@@ -393,6 +397,8 @@ int kv_fwd_bwd_ex(const kv_args* a)
         default: return dispatch_deriv<32>(p, a->dtype, deriv, s);
     }
 }
+
+extern "C" {
 
 static int core_call(const void* v, const void* x, void* logk, void* dv, void* dx, int64_t n,
                      int bins, int dtype, void* stream)
@@ -538,9 +544,10 @@ int kv_sum(const void* a, int64_t n, int dtype, double* out, void* stream)
     return KV_OK;
 }
 
-// Host-buffer form: chunks alternate between the caller's stream and an internal one; each
-// stream copies its chunk in, computes it and copies it out in order, so the copies of one
-// stream overlap the kernels of the other.
+// Host-buffer form: chunks of up to 2^20 pairs rotate over three streams (the caller's and two
+// internal ones); each stream copies its chunk in, computes it and copies it out in order, so
+// one chunk's input copy, another's kernels and a third's output copy run at the same time.
+// Device buffers (and the learned path's fallback lists) are allocated once per call.
 int kv_fwd_bwd_host(const kv_args* h)
 {
     if (!h) return KV_ERR_NULL;
@@ -552,30 +559,34 @@ int kv_fwd_bwd_host(const kv_args* h)
     const int64_t n = h->n;
     if (n == 0) return KV_OK;
     const size_t es = kvh::elem_size(h->dtype);
-    const int64_t chunk = n < (int64_t)(1 << 22) ? n : (int64_t)(1 << 22);
-    const int nslots = n > chunk ? 2 : 1;
-    cudaStream_t st[2];
-    st[0] = (cudaStream_t)h->stream;
-    st[1] = nullptr;
-    if (nslots == 2) KV_CUDA_TRY(cudaStreamCreateWithFlags(&st[1], cudaStreamNonBlocking));
-    char* buf[2] = {nullptr, nullptr};
+    const int64_t chunk = n < (int64_t)(1 << 20) ? n : (int64_t)(1 << 20);
+    const int64_t nchunks = (n + chunk - 1) / chunk;
+    const int nslots = nchunks < 3 ? (int)nchunks : 3;
+    const bool mlp = h->bracket == KV_BRACKET_MLP;
+    const size_t slot_bytes = 5 * es * chunk + (mlp ? sizeof(uint32_t) * (chunk + 32) : 0);
+    cudaStream_t st[3] = {(cudaStream_t)h->stream, nullptr, nullptr};
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < nslots && e == cudaSuccess; ++k)
-        e = cudaMallocAsync((void**)&buf[k], 5 * es * chunk, st[0]);
-    cudaEvent_t ready = nullptr;
-    if (e == cudaSuccess && nslots == 2) {
-        e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventRecord(ready, st[0]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st[1], ready, 0);
+    for (int k = 1; k < nslots && e == cudaSuccess; ++k)
+        e = cudaStreamCreateWithFlags(&st[k], cudaStreamNonBlocking);
+    char* buf = nullptr;
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&buf, slot_bytes * nslots, st[0]);
+    cudaEvent_t ev = nullptr;
+    if (e == cudaSuccess && nslots > 1) {
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, st[0]);
+        for (int k = 1; k < nslots && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(st[k], ev, 0);
     }
-    for (int64_t off = 0, c = 0; e == cudaSuccess && rc == KV_OK && off < n; off += chunk, ++c) {
+    for (int64_t c = 0; e == cudaSuccess && rc == KV_OK && c < nchunks; ++c) {
         const int k = (int)(c % nslots);
+        const int64_t off = c * chunk;
         const int64_t m = (n - off) < chunk ? (n - off) : chunk;
-        char* dvin = buf[k];
-        char* dxin = dvin + es * chunk;
-        char* dl = dvin + 2 * es * chunk;
-        char* ddv = dvin + 3 * es * chunk;
-        char* ddx = dvin + 4 * es * chunk;
+        char* base = buf + slot_bytes * k;
+        char* dvin = base;
+        char* dxin = base + es * chunk;
+        char* dl = base + 2 * es * chunk;
+        char* ddv = base + 3 * es * chunk;
+        char* ddx = base + 4 * es * chunk;
+        uint32_t* scratch = mlp ? (uint32_t*)(base + 5 * es * chunk) : nullptr;
         e = cudaMemcpyAsync(dvin, (const char*)h->v + es * off, es * m, cudaMemcpyHostToDevice, st[k]);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(dxin, (const char*)h->x + es * off, es * m, cudaMemcpyHostToDevice,
@@ -589,7 +600,7 @@ int kv_fwd_bwd_host(const kv_args* h)
         d.dx = h->dx ? ddx : nullptr;
         d.n = m;
         d.stream = st[k];
-        rc = kv_fwd_bwd_ex(&d);
+        rc = kvh::fwd_bwd_ex(&d, scratch);
         if (rc != KV_OK) break;
         if (h->logk)
             e = cudaMemcpyAsync((char*)h->logk + es * off, dl, es * m, cudaMemcpyDeviceToHost, st[k]);
@@ -598,21 +609,21 @@ int kv_fwd_bwd_host(const kv_args* h)
         if (e == cudaSuccess && h->dx)
             e = cudaMemcpyAsync((char*)h->dx + es * off, ddx, es * m, cudaMemcpyDeviceToHost, st[k]);
     }
-    // join the second stream back before the buffers go
-    if (nslots == 2 && ready) {
-        cudaError_t e2 = cudaEventRecord(ready, st[1]);
-        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(st[0], ready, 0);
+    // join the internal streams back into the caller's before the buffer goes
+    for (int k = 1; k < nslots && ev; ++k) {
+        cudaError_t e2 = cudaEventRecord(ev, st[k]);
+        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(st[0], ev, 0);
         if (e == cudaSuccess) e = e2;
     }
-    for (int k = 0; k < nslots; ++k)
-        if (buf[k]) {
-            cudaError_t e2 = cudaFreeAsync(buf[k], st[0]);
-            if (e == cudaSuccess) e = e2;
-        }
+    if (buf) {
+        cudaError_t e2 = cudaFreeAsync(buf, st[0]);
+        if (e == cudaSuccess) e = e2;
+    }
     cudaError_t e3 = cudaStreamSynchronize(st[0]);
     if (e == cudaSuccess) e = e3;
-    if (ready) cudaEventDestroy(ready);
-    if (st[1]) cudaStreamDestroy(st[1]);
+    if (ev) cudaEventDestroy(ev);
+    for (int k = 1; k < nslots; ++k)
+        if (st[k]) cudaStreamDestroy(st[k]);
     if (rc != KV_OK) return rc;
     if (e != cudaSuccess) return kvh::cuda_fail(e);
     return KV_OK;

@@ -40,13 +40,18 @@ struct MlpView {
     const float* w3;            // [2][64]
     const float* b3;            // [2]
     float in_scale[4];          // a = asinh(v * in_scale[0]) * in_scale[1], b = log x * in_scale[2] + in_scale[3]
-    float out_scale[4];         // t0 = y0 * out_scale[0] + out_scale[1], width = softplus(y1) * out_scale[2]
+    float out_scale[4];         // log half-widths L_k = y_k * out_scale[2k] + out_scale[2k+1]
 };
 
 // Fills a view of the handle's inference weights; returns KV_OK or KV_ERR_HANDLE.
 int mlp_view(const kv_mlp* h, MlpView* out);
 
-// Launches the learned-bracket kernel (kv_mlp.cu).  Arguments are already validated.
-int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter);
+// Launches the learned-bracket kernels (kv_mlp.cu).  Arguments are already validated.
+// `scratch`: NULL, or device memory for n + 32 uint32 (the fallback list), reused across calls
+// on the same stream; NULL allocates it on the stream for this call.
+int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, uint32_t* scratch);
+
+// kv_fwd_bwd_ex with an optional preallocated learned-path scratch (see launch_mlp_path).
+int fwd_bwd_ex(const kv_args* a, uint32_t* scratch);
 
 }  // namespace kvh

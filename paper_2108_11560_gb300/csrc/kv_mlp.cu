@@ -879,7 +879,7 @@ int mlp_view(const kv_mlp* h, MlpView* out)
     return KV_OK;
 }
 
-int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter)
+int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, uint32_t* scratch_in)
 {
     if (a->n > (int64_t)0xffffffffll) return KV_ERR_SIZE;
     MlpPathParams p;
@@ -896,9 +896,9 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter)
     p.bins = bins;
     p.log_eps = (float)log_eps;
     cudaStream_t s = (cudaStream_t)a->stream;
-    // scratch: the fallback list and its counter
-    uint32_t* scratch = nullptr;
-    KV_CUDA_TRY(cudaMallocAsync((void**)&scratch, sizeof(uint32_t) * (a->n + 32), s));
+    // scratch: the fallback list and its counter (the caller's, or allocated on the stream)
+    uint32_t* scratch = scratch_in;
+    if (!scratch) KV_CUDA_TRY(cudaMallocAsync((void**)&scratch, sizeof(uint32_t) * (a->n + 32), s));
     p.fb_count = scratch;
     p.fb_list = scratch + 32;
     cudaError_t e = cudaMemsetAsync(p.fb_count, 0, sizeof(uint32_t), s);
@@ -926,7 +926,7 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter)
         note_launch();
         e = cudaGetLastError();
     }
-    cudaError_t e2 = cudaFreeAsync(scratch, s);
+    cudaError_t e2 = scratch_in ? cudaSuccess : cudaFreeAsync(scratch, s);
     if (e != cudaSuccess) return cuda_fail(e);
     if (e2 != cudaSuccess) return cuda_fail(e2);
     return KV_OK;
