@@ -62,6 +62,48 @@ def build() -> None:
         _lib(key)
 
 
+def compile_variant_source(src_path: str, out_dir: str) -> dict:
+    """Compile another copy of the oracle source (both precisions) into out_dir and return the
+    loaded libraries, for tests that plant mistakes in a copy and check that the pins catch
+    them.  Use with `swap_libraries`."""
+    libs = {}
+    for key, (name, defines) in _VARIANTS.items():
+        out = os.path.join(out_dir, name)
+        subprocess.run(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-fopenmp", *defines, src_path,
+                        "-o", out, "-lm"], check=True)
+        libs[key] = out
+    return libs
+
+
+class swap_libraries:
+    """Context manager: the oracle functions use the given compiled copies instead of the
+    package's own library (test infrastructure for planted-mistake checks)."""
+
+    def __init__(self, paths: dict):
+        self.paths = paths
+        self.saved = None
+
+    def __enter__(self):
+        with _LOCK:
+            self.saved = dict(_LIBS)
+        build()
+        saved_compile = globals()["_compile"]
+        try:
+            globals()["_compile"] = lambda name, defines: self.paths["long" if "ld" in name else "double"]
+            with _LOCK:
+                _LIBS.clear()
+            for key in _VARIANTS:
+                _lib(key)
+        finally:
+            globals()["_compile"] = saved_compile
+        return self
+
+    def __exit__(self, *exc):
+        with _LOCK:
+            _LIBS.clear()
+            _LIBS.update(self.saved)
+
+
 def _lib(precision: str) -> ctypes.CDLL:
     with _LOCK:
         if precision not in _LIBS:

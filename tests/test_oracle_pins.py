@@ -230,6 +230,38 @@ def test_bruteforce_trapezoid_long_double():
             assert rel(out["dv"], ref_dv)[0] < 1e-13, (v, x)
 
 
+@pytest.mark.parametrize("bins, log_eps", [(1, -3.0), (2, -3.0), (5, -8.0), (128, oracle.LOG_EPS_F64)])
+def test_fixed_bins_on_returned_bracket_match_library_trapezoid(bins, log_eps):
+    """Eq. (int) given the bracket: on the [t0, t1] that the oracle returns, log K and the two
+    derivative ratios equal scipy's composite trapezoid over bins + 1 equally spaced points
+    (bins = 1 is the textbook two-point rule).  With a coarse eps the range end matters, so a
+    wrong bin width or a dropped end weight shows even where the integrand is tiny."""
+    import scipy.integrate
+    v, x = W.full_domain(40, seed=111)
+    v = np.concatenate([v, [0.0, 0.5, 30.0]])
+    x = np.concatenate([x, [2.0, 0.1, 40.0]])
+    out = oracle.o1(v, x, bins=bins, log_eps=log_eps, precision="long", bracket=True)
+    ld = np.longdouble
+    for i in range(v.size):
+        t0, t1 = ld(out["t0"][i]), ld(out["t1"][i])
+        if not t1 > t0:
+            continue
+        t = t0 + (t1 - t0) * np.arange(bins + 1, dtype=ld) / ld(bins)
+        a = np.abs(ld(v[i]) * t)
+        g = a + np.log1p(np.exp(-2 * a)) - np.log(ld(2)) - ld(x[i]) * np.cosh(t)
+        gm = g.max()
+        w = np.exp(g - gm)
+        s0 = scipy.integrate.trapezoid(w, t)
+        ref_l = float(gm + np.log(s0))
+        ref_dv = float(scipy.integrate.trapezoid(w * t * np.tanh(ld(v[i]) * t), t) / s0)
+        ref_dx = float(-scipy.integrate.trapezoid(w * np.cosh(t), t) / s0)
+        # t0, t1 come back rounded to FP64: the points above are those rounded ends
+        assert rel_logk(out["logk"][i:i + 1], ref_l)[0] < 1e-12, (v[i], x[i])
+        assert rel(out["dx"][i:i + 1], ref_dx)[0] < 1e-11, (v[i], x[i])
+        if v[i] > 0:
+            assert rel(out["dv"][i:i + 1], ref_dv)[0] < 1e-11, (v[i], x[i])
+
+
 def test_o1_against_dense_full_domain():
     """The method at 128 bins against the dense quadrature on the whole target domain."""
     v, x = W.full_domain(2000, seed=106)
@@ -305,6 +337,26 @@ def test_findrange_and_findzero_alone():
         gpp = oracle.g_eval(v, x, [tp], precision="long")[2][0]
         assert gp(tp) <= 4 * np.spacing(tp) * abs(gpp) and tp >= root - 4 * np.spacing(root)
         assert tp - root <= (neg - pos) * 2.0 ** -10
+
+
+def test_findzero_keeps_the_zero_bracketed():
+    """Algorithm 2 on h = g - G - log eps from a negative end just above 0, where h' is tiny
+    and a full Newton step lands far beyond the bracket: the result stays in the initial
+    bracket, on its negative side, within 2^-10 of its width of the zero there (brentq)."""
+    le = oracle.LOG_EPS_F64
+    for v, x in [(1000.0, 1.0), (50.0, 0.01), (300.0, 20.0), (5.0, 1e-4)]:
+        o = oracle.o1([v], [x], precision="long", bracket=True)
+        tp, G = o["tp"][0], o["G"][0]
+        for t_neg in (1e-8, 1e-5):
+            h = lambda t: oracle.g_eval(v, x, [t], precision="long")[0][0] - G - le
+            assert h(t_neg) < 0 < h(tp)
+            _, _, z = oracle.alg12(v, x, 1, 0.0, t_neg, tp, G=G, log_eps=le, precision="long")
+            r = scipy.optimize.brentq(h, t_neg, tp, xtol=1e-15)
+            assert t_neg <= z <= tp, (v, x, t_neg, z)
+            # z comes back rounded to FP64: allow that rounding on the negative side
+            slope = abs(oracle.g_eval(v, x, [z], precision="long")[1][0])
+            assert h(z) <= 4 * np.spacing(z) * slope, (v, x, t_neg, z)
+            assert r - z <= (tp - t_neg) * 2.0 ** -10, (v, x, t_neg, z, r)
 
 
 def test_stopping_rule_reading():
