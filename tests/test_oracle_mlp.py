@@ -89,6 +89,11 @@ def test_batch_indices_in_range_and_spread():
     idx = mlp.batch_indices(7, 3, 4096, 1000)
     assert idx.min() >= 0 and idx.max() < 1000
     assert len(np.unique(idx)) > 950
+    # consecutive steps draw different samples; twenty small batches cover nearly the whole set
+    a, b = mlp.batch_indices(7, 0, 64, 1000), mlp.batch_indices(7, 1, 64, 1000)
+    assert len(np.intersect1d(a, b)) < 20
+    seen = np.unique(np.concatenate([mlp.batch_indices(7, j, 256, 1000) for j in range(20)]))
+    assert len(seen) > 990
 
 
 def test_training_reduces_loss():

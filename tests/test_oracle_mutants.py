@@ -1,7 +1,8 @@
-"""Planted mistakes: each mutant is a copy of the oracle's C source with one plausible slip
-(a dropped endpoint weight, a sign, a wrong end returned by FindZero, a missing factor in a
-derivative integrand, ...).  Every mutant must fail at least one of the pins in
-test_oracle_pins.py, which shows the pins constrain every part of the oracle.  Runs on the CPU."""
+"""Planted mistakes: each mutant is a copy of the oracle's C source (or of its MLP module) with
+one plausible slip (a dropped endpoint weight, a sign, a wrong end returned by FindZero, a missing
+factor in a derivative integrand, a transposed weight in the backward pass, ...).  Every mutant
+must fail at least one of the pins in test_oracle_pins.py / test_oracle_mlp.py, which shows the
+pins constrain every part of the oracle.  Runs on the CPU."""
 import json
 import os
 import shutil
@@ -116,3 +117,60 @@ def test_every_planted_mistake_is_caught(name, old, new):
         shutil.rmtree(d, ignore_errors=True)
     # the real oracle is back in place
     pins.test_half_integer_closed_form(0)
+
+
+# ------------------------------------------------------------------ the learned-bracket oracle
+
+MLP_SRC = os.path.join(os.path.dirname(oracle.__file__), "mlp.py")
+
+MLP_MUTANTS = [
+    ("backward through W2 transposed", 'dz1 = (dz2 @ P["W2"])', 'dz1 = (dz2 @ P["W2"].T)'),
+    ("layer-2 ReLU mask from layer 1", '* (F["z2"] > 0)', '* (F["z1"] > 0)'),
+    ("b1 gradient from layer 2", 'g["b1"] = dz1.sum(0)', 'g["b1"] = dz2.sum(0)'),
+    ("W1 gradient with the features swapped", 'g["W1"] = dz1.T @ F["f"]', 'g["W1"] = dz1.T @ F["f"][:, ::-1]'),
+    ("loss not halved", "loss = 0.5 * np.sum(r * r) / B", "loss = np.sum(r * r) / B"),
+    ("Adam without bias correction", "mh = m / (1 - beta1 ** step)", "mh = m"),
+    ("Adam second moment of |g|", "s = beta2 * s + (1 - beta2) * g * g", "s = beta2 * s + (1 - beta2) * np.abs(g)"),
+    ("Adam steps uphill", "return p - lr * mh", "return p + lr * mh"),
+    ("target L1 measured from t0", "L1 = np.log(np.maximum(np.asarray(t1) - np.asarray(tp), 0.0) + DELTA)",
+     "L1 = np.log(np.maximum(np.asarray(t1) - np.asarray(t0), 0.0) + DELTA)"),
+    ("predict scales L1 like L0", "L1 = y[:, 1] * OUT_SCALE[2] + OUT_SCALE[3]", "L1 = y[:, 1] * OUT_SCALE[0] + OUT_SCALE[1]"),
+    ("predict keeps DELTA", "t1 = t_ref + np.maximum(np.exp(L1) - DELTA, 0.0)", "t1 = t_ref + np.exp(L1)"),
+    ("peak Newton step with the wrong sign", "t = np.clip(t - step, 0.0, t)", "t = np.clip(t + step, 0.0, t)"),
+    ("SplitMix64 last shift 33", "return z ^ (z >> 31)", "return z ^ (z >> 33)"),
+    ("batch indices ignore the step", "mix64((seed + step * batch + k) & MASK64)", "mix64((seed + k) & MASK64)"),
+]
+
+
+def _mlp_pins():
+    import test_oracle_mlp as t
+    return t, [getattr(t, name) for name in dir(t) if name.startswith("test_")]
+
+
+@pytest.mark.parametrize("name, old, new", MLP_MUTANTS, ids=[m[0] for m in MLP_MUTANTS])
+def test_every_planted_mlp_mistake_is_caught(name, old, new):
+    import types
+    src = open(MLP_SRC).read()
+    assert src.count(old) == 1, name
+    mod = types.ModuleType("oracle.mlp_mutant")
+    exec(compile(src.replace(old, new), MLP_SRC, "exec"), mod.__dict__)
+    t, tests = _mlp_pins()
+    saved = t.mlp
+    t.mlp = mod
+    caught = False
+    try:
+        for pin in tests:
+            try:
+                pin()
+            except Exception:
+                caught = True
+                break
+    finally:
+        t.mlp = saved
+    assert caught, f"no pin catches: {name}"
+
+
+def test_mlp_pins_pass_on_the_oracle_itself():
+    _, tests = _mlp_pins()
+    for pin in tests:
+        pin()
