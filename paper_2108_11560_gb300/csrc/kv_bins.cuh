@@ -187,52 +187,87 @@ __device__ __forceinline__ float delta_g_slope_f32(const BinsF& b, float e2, flo
     return b.c1 + dl - b.ap * (es - 1.0f) + b.am * (ems - 1.0f);
 }
 
-// One FP32 bin: its weight c_m e^{g(t_m) - g(t_p)} and the two derivative integrands' weights.
-template <bool DERIV>
-__device__ __forceinline__ void bin_f32(const BinsF& b, int m, float& w, float& w1, float& w2)
+// The bin constants rescaled once per pair so that a bin works in base-2 exponent units: the
+// weight's exponent (g(t) - g(t_p)) log2 e goes straight into ex2.
+struct BinsK {
+    float c1, ap, am, lu;  // v - x sinh t_p, x e^{+-t_p}/2, log1p(e^{-2u}), each times log2 e
+    float hep, hem;        // e^{+-t_p} / 2
+};
+
+__device__ __forceinline__ BinsK bins_k(const BinsF& b)
 {
-    const float s = fmaf((float)m, b.h, b.s0);
+    BinsK k;
+    k.c1 = b.c1 * LOG2E_F;
+    k.ap = b.ap * LOG2E_F;
+    k.am = b.am * LOG2E_F;
+    k.lu = b.lu * LOG2E_F;
+    k.hep = 0.5f * b.ep;
+    k.hem = 0.5f * b.em;
+    return k;
+}
+
+// vt below this uses tanh_small
+constexpr float TANH_SERIES_MAX = 0.625f;
+
+// One FP32 bin at m = mf (a float holding a small integer, exact): its weight c e^{g(t_m) - g(t_p)}
+// and the two derivative integrands' weights.  With VOTE (all 32 lanes of the warp run the same
+// bins together) the series for tanh(vt) is evaluated only when some lane of the warp needs it.
+template <bool DERIV, bool VOTE>
+__device__ __forceinline__ void bin_f32(const BinsF& b, const BinsK& k, float mf, float c, float& w,
+                                        float& w1, float& w2)
+{
+    const float s = fmaf(mf, b.h, b.s0);
     float php, phm, es, ems;
     phi_pair(s, php, phm, es, ems);
     const float vt = fmaf(b.v, s, b.u);
-    const float e2 = ex2_approx(-2.0f * LOG2E_F * vt);             // e^{-2vt}
-    const float d = fmaf(lg2_approx(1.0f + e2), LN2_F, -b.lu);      // log1p(e^{-2vt}) - log1p(e^{-2u})
-    const float dg = fmaf(b.c1, s, d) - fmaf(b.ap, php, b.am * phm);
-    const float c = (m == 0 || m == b.n) ? 0.5f : 1.0f;
-    w = c * ex2_approx(dg * LOG2E_F);
+    const float e2 = ex2_approx(-2.0f * LOG2E_F * vt);     // e^{-2vt}
+    const float d = lg2_approx(1.0f + e2) - k.lu;          // [log1p(e^{-2vt}) - log1p(e^{-2u})] log2 e
+    const float dg = fmaf(k.c1, s, d) - fmaf(k.ap, php, k.am * phm);
+    w = c * ex2_approx(dg);
     if (DERIV) {
         const float t = b.tp + s;
-        const float th = fabsf(vt) < 0.625f ? tanh_small(vt)
-                                            : (1.0f - e2) * rcp_approx(1.0f + e2);  // tanh(vt)
+        float th = (1.0f - e2) * rcp_approx(1.0f + e2);  // tanh(vt)
+        const bool small = vt < TANH_SERIES_MAX;
+        if (!VOTE || __any_sync(0xffffffffu, small))
+            th = small ? tanh_small(vt) : th;
         w1 = w * (t * th);
-        w2 = w * (0.5f * fmaf(b.ep, es, b.em * ems));                 // cosh t
+        w2 = w * fmaf(k.hep, es, k.hem * ems);  // w cosh t
     }
 }
 
-// The three sums, compensated per block of four bins: a block's four terms are added pairwise
-// (two rounding levels) and the block sum goes into a Kahan sum, so the relative error stays
-// a few units of 2^-24 for any bin count at 1.75 additions per term instead of Kahan's four.
-template <int L, bool DERIV>
+// The three sums over bins m = lane, lane + L, ... <= n, compensated per block of four bins: a
+// block's four terms are added pairwise (two rounding levels) and the block sum goes into a Kahan
+// sum, so the relative error stays a few units of 2^-24 for any bin count at 1.75 additions per
+// term instead of Kahan's four.  The end weight 1/2 of bin 0 is applied to the first block's
+// first term (lane 0 only); bin n always falls in the tail loop, which selects its weight.
+// VOTE requires L = 1 and all 32 lanes of the warp in the call with the same n.
+template <int L, bool DERIV, bool VOTE = false>
 __device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, float& S1, float& S2)
 {
+    static_assert(!VOTE || L == 1, "the warp vote needs every lane on the same bins");
+    const BinsK k = bins_k(b);
     KahanSum<float> k0, k1, k2;
     k0.init();
     k1.init();
     k2.init();
     int m = lane;
-    for (; m + 3 * L <= b.n; m += 4 * L) {
+    float mf = (float)lane;
+    float c_first = lane == 0 ? 0.5f : 1.0f;
+    for (; m + 3 * L < b.n; m += 4 * L, mf += (float)(4 * L)) {
         float w[4], w1[4], w2[4];
+        bin_f32<DERIV, VOTE>(b, k, mf, c_first, w[0], w1[0], w2[0]);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) bin_f32<DERIV>(b, m + q * L, w[q], w1[q], w2[q]);
+        for (int q = 1; q < 4; ++q) bin_f32<DERIV, VOTE>(b, k, mf + (float)(q * L), 1.0f, w[q], w1[q], w2[q]);
+        c_first = 1.0f;
         k0.add((w[0] + w[1]) + (w[2] + w[3]));
         if (DERIV) {
             k1.add((w1[0] + w1[1]) + (w1[2] + w1[3]));
             k2.add((w2[0] + w2[1]) + (w2[2] + w2[3]));
         }
     }
-    for (; m <= b.n; m += L) {
+    for (; m <= b.n; m += L, mf += (float)L) {
         float w, w1, w2;
-        bin_f32<DERIV>(b, m, w, w1, w2);
+        bin_f32<DERIV, VOTE>(b, k, mf, (m == 0 || m == b.n) ? 0.5f : 1.0f, w, w1, w2);
         k0.add(w);
         if (DERIV) {
             k1.add(w1);

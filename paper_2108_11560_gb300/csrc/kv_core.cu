@@ -16,6 +16,15 @@
 
 #include <atomic>
 
+// The host-buffer entry point streams 2^KV_HOST_CHUNK_LOG2 pairs per chunk through
+// KV_HOST_SLOTS device buffer slots, one stream each (copy in, compute, copy out).
+#ifndef KV_HOST_CHUNK_LOG2
+#define KV_HOST_CHUNK_LOG2 19
+#endif
+#ifndef KV_HOST_SLOTS
+#define KV_HOST_SLOTS 4
+#endif
+
 namespace {
 thread_local char g_last_cuda_error[256] = "";
 std::atomic<uint64_t> g_launches{0};
@@ -559,12 +568,12 @@ int kv_fwd_bwd_host(const kv_args* h)
     const int64_t n = h->n;
     if (n == 0) return KV_OK;
     const size_t es = kvh::elem_size(h->dtype);
-    const int64_t chunk = n < (int64_t)(1 << 20) ? n : (int64_t)(1 << 20);
+    const int64_t chunk = n < ((int64_t)1 << KV_HOST_CHUNK_LOG2) ? n : ((int64_t)1 << KV_HOST_CHUNK_LOG2);
     const int64_t nchunks = (n + chunk - 1) / chunk;
-    const int nslots = nchunks < 3 ? (int)nchunks : 3;
+    const int nslots = nchunks < KV_HOST_SLOTS ? (int)nchunks : KV_HOST_SLOTS;
     const bool mlp = h->bracket == KV_BRACKET_MLP;
     const size_t slot_bytes = 5 * es * chunk + (mlp ? sizeof(uint32_t) * (chunk + 32) : 0);
-    cudaStream_t st[3] = {(cudaStream_t)h->stream, nullptr, nullptr};
+    cudaStream_t st[KV_HOST_SLOTS] = {(cudaStream_t)h->stream};
     cudaError_t e = cudaSuccess;
     for (int k = 1; k < nslots && e == cudaSuccess; ++k)
         e = cudaStreamCreateWithFlags(&st[k], cudaStreamNonBlocking);

@@ -132,13 +132,27 @@ int alloc_handle(kv_mlp** out)
 
 // ------------------------------------------------------------------ device pieces
 
+// asinh(z) for z >= 0 as ln(z + sqrt(z^2 + 1)) with the approximate logarithm and reciprocal
+// square root: absolute error a few 1e-7 (relative error grows as z -> 0, where the result is
+// tiny).  Used for the network's order feature and the start of the peak search, neither of which
+// needs more.
+__device__ __forceinline__ float fast_asinh(float z)
+{
+    if (z > 1e18f) return __logf(2.0f * z);
+    const float q = fmaf(z, z, 1.0f);
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(q));
+    return __logf(fmaf(q, r, z));
+}
+
 // The peak of g by four FP32 Newton steps from asinh(v/x) (0 when v^2 <= x).  Its accuracy does
 // not enter the results (the bins are exact relative to any reference point near the peak), so
-// the steps use the approximate exponential, reciprocal and division.
+// the steps use the approximate exponential, reciprocal and division.  The start is nudged up so
+// that it stays on the side of the zero where g' <= 0 despite the approximate asinh.
 __device__ __forceinline__ float peak_f32(float v, float x)
 {
     if (!(v * v > x)) return 0.0f;
-    float t = asinhf(v / x);
+    float t = fast_asinh(__fdividef(v, x)) * (1.0f + 0x1.0p-16f);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         float e2 = ex2_approx(-2.0f * LOG2E_F * v * t);
@@ -164,7 +178,7 @@ struct MlpSmem {
 // weights widened to FP32; h1 is rounded to BF16 as the tensor-core form would see it.
 __device__ __forceinline__ void mlp_forward(const MlpSmem& s, float v, float x, float& L0, float& L1)
 {
-    const float a = asinhf(v * s.in_scale[0]) * s.in_scale[1];
+    const float a = fast_asinh(v * s.in_scale[0]) * s.in_scale[1];
     const float b = fmaf(__logf(x), s.in_scale[2], s.in_scale[3]);
     float h1[H];
 #pragma unroll
@@ -211,27 +225,66 @@ __device__ void load_mlp_smem(MlpSmem& s, const kvh::MlpView& m)
     }
 }
 
-// Per-pair constants of the FP32 bins at the reference point tr, with the offset g(tr) as a
-// float-float (no FP64): G = v tr + log1p(e^{-2 v tr}) - ln 2 - x cosh tr.
+// The reference point of the bins: t_r = j ln2/128, the grid point nearest the peak estimate.
+// On this grid e^{+-t_r} = 2^{+-(j >> 7)} 2^{+-(j & 127)/128} come exactly (as float-floats) from
+// a 128-entry table, so the constants whose inputs cancel need no extended-precision exponential.
+// |t_r - t_p| <= ln2/256 = 0.0027, and the bins are exact relative to any reference point.
+constexpr int kGridBits = 7;
+constexpr float kGridInv = 184.6649652337873f;         // 128 / ln2
+constexpr float kGridStepHi = 5.415212363e-03f;        // ln2 / 128 rounded
+constexpr float kGridStepLo = -1.488011103e-11f;       // ln2 / 128 - kGridStepHi
+
+struct ExpTable {
+    float4 e[1 << kGridBits];  // {hi, lo} of 2^{i/128}, then {hi, lo} of 2^{-i/128}
+};
+
+const ExpTable& exp_table()
+{
+    static const ExpTable t = [] {
+        ExpTable r;
+        for (int i = 0; i < (1 << kGridBits); ++i) {
+            const double p = exp2((double)i / (1 << kGridBits)), m = exp2(-(double)i / (1 << kGridBits));
+            const float ph = (float)p, mh = (float)m;
+            r.e[i] = make_float4(ph, (float)(p - ph), mh, (float)(m - mh));
+        }
+        return r;
+    }();
+    return t;
+}
+
+// 2^k for |k| <= 126 (exact); larger |k| saturates (inf or the smallest normal).
+__device__ __forceinline__ float pow2i(int k)
+{
+    return __int_as_float(min(max(k + 127, 1), 254) << 23);
+}
+
+// Per-pair constants of the FP32 bins at the reference point t_r, with the offset g(t_r) as a
+// float-float (no FP64): G = v t_r + log1p(e^{-2 v t_r}) - ln 2 - x cosh t_r.
 struct PeakConst {
     df G;
     BinsF b;
 };
 
-__device__ __forceinline__ PeakConst peak_constants(float v, float x, float tr)
+__device__ __forceinline__ PeakConst peak_constants(float v, float x, float tp, const float4* tab)
 {
     PeakConst c;
-    df E = df_exp(tr);
-    df Ei = df_rcp(E);
-    df u = two_prod(v, tr);
-    float lu = log1pf(expf(-2.0f * u.hi));
-    df ch = df_mul_f(df_add(E, Ei), 0.5f * x);  // x cosh tr
-    df sh = df_mul_f(df_sub(E, Ei), 0.5f * x);  // x sinh tr
-    c.G = df_sub(df_add(df_add(u, df_make(lu)), df_neg(df_ln2())), ch);
-    df c1 = df_sub(df_make(v), sh);
+    const float j = rintf(tp * kGridInv);
+    const int ji = (int)j;
+    const float4 T = tab[ji & ((1 << kGridBits) - 1)];
+    const float p2 = pow2i(ji >> kGridBits), p2i = pow2i(-(ji >> kGridBits));
+    const df E{T.x * p2, T.y * p2}, Ei{T.z * p2i, T.w * p2i};  // e^{t_r}, e^{-t_r}
+    df tr = two_prod(j, kGridStepHi);
+    tr = fast_two_sum(tr.hi, fmaf(j, kGridStepLo, tr.lo));
+    df u = two_prod(v, tr.hi);
+    u = fast_two_sum(u.hi, fmaf(v, tr.lo, u.lo));
+    const float lu = log1pf(expf(-2.0f * u.hi));
+    const df ch = df_mul_f(df_add_fast(E, Ei), 0.5f * x);  // x cosh t_r
+    const df sh = df_mul_f(df_sub_fast(E, Ei), 0.5f * x);  // x sinh t_r
+    c.G = df_sub_fast(df_add_fast(df_add_fast(u, df_make(lu)), df_neg(df_ln2())), ch);
+    const df c1 = df_sub_fast(df_make(v), sh);
     c.b.v = v;
     c.b.u = u.hi;
-    c.b.tp = tr;
+    c.b.tp = tr.hi;
     c.b.c1 = c1.hi + c1.lo;
     c.b.ap = 0.5f * x * E.hi;
     c.b.am = 0.5f * x * Ei.hi;
@@ -255,6 +308,7 @@ struct MlpPathParams {
     uint32_t* fb_list;
     uint32_t* fb_count;
     kvh::MlpView mlp;
+    ExpTable exp_tab;
 };
 
 constexpr int kMlpBlock = 128;
@@ -362,6 +416,7 @@ struct TcSmem {
     unsigned char b[H * H * 2];    // W2 (BF16), row = output unit, K = input unit
     float w1[2 * H], b1[H], b2[H], w3[2 * H], b3[2];
     float in_scale[4], out_scale[4];
+    float4 exp_tab[1 << kGridBits];
     uint64_t mbar;
     uint32_t tmem;
 };
@@ -397,6 +452,7 @@ __global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
     }
     for (int k = t; k < H * H; k += kMlpBlock)
         *reinterpret_cast<unsigned short*>(sm.b + tile_off(k / H, k % H)) = p.mlp.w2h[k];
+    for (int k = t; k < (1 << kGridBits); k += kMlpBlock) sm.exp_tab[k] = p.exp_tab.e[k];
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.mbar)));
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -426,7 +482,7 @@ __global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
         const float xa = edge ? 1.0f : x;
         // layer 1 -> BF16 row t of the A tile
         {
-            const float a = asinhf(va * sm.in_scale[0]) * sm.in_scale[1];
+            const float a = fast_asinh(va * sm.in_scale[0]) * sm.in_scale[1];
             const float b = fmaf(__logf(xa), sm.in_scale[2], sm.in_scale[3]);
 #pragma unroll
             for (int c = 0; c < H / 8; ++c) {
@@ -434,10 +490,10 @@ __global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int u0 = 8 * c + 2 * q, u1 = u0 + 1;
-                    float z0 = fmaxf(fmaf(sm.w1[2 * u0], a, fmaf(sm.w1[2 * u0 + 1], b, sm.b1[u0])), 0.0f);
-                    float z1 = fmaxf(fmaf(sm.w1[2 * u1], a, fmaf(sm.w1[2 * u1 + 1], b, sm.b1[u1])), 0.0f);
-                    __nv_bfloat162 hv = __floats2bfloat162_rn(z0, z1);
-                    packed[q] = *reinterpret_cast<uint32_t*>(&hv);
+                    const float z0 = fmaf(sm.w1[2 * u0], a, fmaf(sm.w1[2 * u0 + 1], b, sm.b1[u0]));
+                    const float z1 = fmaf(sm.w1[2 * u1], a, fmaf(sm.w1[2 * u1 + 1], b, sm.b1[u1]));
+                    // relu and round to BF16 in one conversion (unit u0 in the low half)
+                    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(packed[q]) : "f"(z1), "f"(z0));
                 }
                 *reinterpret_cast<uint4*>(sm.a + tile_off(t, 8 * c)) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
             }
@@ -498,11 +554,13 @@ __global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
         // separately, once per group.
         const float L0 = fmaf(y0, sm.out_scale[0], sm.out_scale[1]);
         const float L1 = fmaf(y1, sm.out_scale[2], sm.out_scale[3]);
-        const float tr = peak_f32(va, xa);
-        const float w0 = fmaxf(__expf(L0) - DELTA, 0.0f);
-        const float w1 = fmaxf(__expf(L1) - DELTA, 1e-6f * (1.0f + tr));
+        const float tp = peak_f32(va, xa);
+        PeakConst c = peak_constants(va, xa, tp, sm.exp_tab);
+        const float tr = c.b.tp;  // the grid point next to tp: the bins' reference
+        // the predicted range [tp - w0, tp + w1] as distances below and above tr
+        const float w0 = fmaxf(fmaxf(__expf(L0) - DELTA, 0.0f) - (tp - tr), 0.0f);
+        const float w1 = fmaxf(fmaxf(__expf(L1) - DELTA, 0.0f) + (tp - tr), 1e-6f * (1.0f + tr));
         float t0, t1;
-        PeakConst c = peak_constants(va, xa, tr);
         const bool ok = check_range(c.b, tr, w0, w1, p.log_eps, lo_ok, t0, t1);
         const bool regular = active && !edge;
         if (regular && !ok) {
@@ -518,7 +576,7 @@ __global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
         c.b.h = (t1 - t0) / (float)p.bins;
         c.b.n = p.bins;
         float S0, S1, S2;
-        sums_f32<1, DERIV>(c.b, 0, S0, S1, S2);
+        sums_f32<1, DERIV, true>(c.b, 0, S0, S1, S2);
         if (regular && ok) {
             df L = df_add(c.G, df_make(logf(c.b.h * S0)));
             lk = L.hi + L.lo;
@@ -895,6 +953,7 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
     p.n = a->n;
     p.bins = bins;
     p.log_eps = (float)log_eps;
+    p.exp_tab = exp_table();
     cudaStream_t s = (cudaStream_t)a->stream;
     // scratch: the fallback list and its counter (the caller's, or allocated on the stream)
     uint32_t* scratch = scratch_in;
