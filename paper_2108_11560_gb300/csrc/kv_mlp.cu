@@ -175,7 +175,8 @@ struct MlpSmem {
 };
 
 // Forward pass of one pair on the CUDA cores: log half-widths (L0, L1).  W2 holds the BF16
-// weights widened to FP32; h1 is rounded to BF16 as the tensor-core form would see it.
+// weights widened to FP32; h1 is rounded to BF16 as the tensor-core form sees it (b2, which the
+// tensor-core form splits into two BF16 parts, stays FP32 here).
 __device__ __forceinline__ void mlp_forward(const MlpSmem& s, float v, float x, float& L0, float& L1)
 {
     const float a = fast_asinh(v * s.in_scale[0]) * s.in_scale[1];
@@ -198,7 +199,7 @@ __device__ __forceinline__ void mlp_forward(const MlpSmem& s, float v, float x, 
             acc = fmaf(w.z, h1[4 * q + 2], acc);
             acc = fmaf(w.w, h1[4 * q + 3], acc);
         }
-        float h2 = fmaxf(acc, 0.0f);
+        const float h2 = fmaxf(acc, 0.0f);
         y0 = fmaf(s.w3[j], h2, y0);
         y1 = fmaf(s.w3[H + j], h2, y1);
     }
@@ -411,40 +412,90 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)
 // group (LBO = 128 B, SBO = 1024 B).
 __device__ __forceinline__ int tile_off(int r, int k) { return (r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
 
+// Offset of element (row r, k) in a K-major slice of 16 columns (two core matrices per 8-row
+// group: LBO = 128 B, SBO = 256 B).
+__device__ __forceinline__ int slice_off(int r, int k) { return (r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+
 struct TcSmem {
-    unsigned char a[128 * H * 2];  // hidden units h1 of the CTA's 128 pairs (BF16)
-    unsigned char b[H * H * 2];    // W2 (BF16), row = output unit, K = input unit
-    float w1[2 * H], b1[H], b2[H], w3[2 * H], b3[2];
+    unsigned char a[128 * H * 2];    // h1, then h2, of the CTA's 128 pairs (BF16, K-major)
+    unsigned char b[H * H * 2];      // W2 (BF16): row = output unit, K = input unit
+    unsigned char bb[H * 16 * 2];    // B of layer 2's extra K slice: k = 0, 1 hold b2 split hi + lo
+    unsigned char ones[8 * 16 * 2];  // A of that slice, one 8-row group read by every group: 1, 1, 0...
+    float w1[2 * H], b1[H], w3[2 * H], b3[2];
     float in_scale[4], out_scale[4];
     float4 exp_tab[1 << kGridBits];
     uint64_t mbar;
     uint32_t tmem;
 };
 
-constexpr uint32_t kTmemCols = 64;
+__device__ __forceinline__ unsigned short bf16_bits(float f) { return __bfloat16_as_ushort(__float2bfloat16_rn(f)); }
+__device__ __forceinline__ float bf16_value(unsigned short h) { return __uint_as_float(((uint32_t)h) << 16); }
+
+// One tcgen05.mma (BF16 inputs, FP32 accumulators in TMEM); acc = 0 overwrites the accumulators.
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar)));
+}
+
+// Waits (bounded) for the mbarrier phase `phase` to complete; false if the limit ran out.
 constexpr int kWaitLimit = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase)
+{
+    uint32_t done = 0;
+    for (int it = 0; it < kWaitLimit && !done; ++it)
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(phase));
+    return done != 0;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(addr));
+}
+
+// Makes this thread's shared-memory tile writes visible to the tensor cores and orders them
+// (and earlier TMEM reads) before the MMA that one thread issues after the barrier.
+__device__ __forceinline__ void sync_for_mma()
+{
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+}
+
+constexpr uint32_t kTmemCols = 64;
 
 // The fast path with the hidden layer on the tensor cores.  Each CTA of 128 threads takes 128
 // pairs per trip (one per thread): layer 1 on the CUDA cores writes h1 as BF16 into a K-major
-// shared tile; one elected thread issues four tcgen05.mma (M = 128, N = 64, K = 16, FP32
-// accumulators in 64 TMEM columns) and commits them to an mbarrier; after the wait, warp w reads
-// TMEM lanes 32w..32w+31 (its own pairs' rows) and finishes layer 3 in registers.  The rest of
-// the pair is as in kv_mlp_kernel.  A wait that does not finish within its limit sends the
-// CTA's remaining pairs to the fallback list (correct, slower) instead of hanging.
+// shared tile; one elected thread issues five tcgen05.mma (M = 128, N = 64, K = 16; the fifth
+// multiplies a column of ones by b2 split into two BF16 parts, so the bias comes out of the
+// tensor cores too) into 64 TMEM columns and commits them to an mbarrier; after the wait, warp w
+// reads TMEM lanes 32w..32w+31 (its own pairs' rows) and finishes layer 3 in registers.  (Layer
+// 3 on the tensor cores as well measured slower: the second MMA round trip per tile costs more
+// than the 128 FMAs it saves.)  A wait that does not finish within its limit sends the CTA's
+// remaining pairs to the fallback list (correct, slower) instead of hanging.
 template <bool DERIV>
 __global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
 {
     __shared__ __align__(1024) TcSmem sm;
     const int t = threadIdx.x;
     const int warp = t >> 5;
-    for (int k = t; k < 2 * H; k += kMlpBlock) {
-        sm.w1[k] = p.mlp.w1[k];
-        sm.w3[k] = p.mlp.w3[k];
-    }
-    for (int k = t; k < H; k += kMlpBlock) {
-        sm.b1[k] = p.mlp.b1[k];
-        sm.b2[k] = p.mlp.b2[k];
-    }
+    for (int k = t; k < 2 * H; k += kMlpBlock) sm.w1[k] = p.mlp.w1[k];
+    for (int k = t; k < H; k += kMlpBlock) sm.b1[k] = p.mlp.b1[k];
     if (t < 2) sm.b3[t] = p.mlp.b3[t];
     if (t < 4) {
         sm.in_scale[t] = p.mlp.in_scale[t];
@@ -452,6 +503,16 @@ __global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
     }
     for (int k = t; k < H * H; k += kMlpBlock)
         *reinterpret_cast<unsigned short*>(sm.b + tile_off(k / H, k % H)) = p.mlp.w2h[k];
+    for (int k = t; k < H * 16; k += kMlpBlock) {  // b2 = hi + lo in BF16 at k = 0, 1
+        const int n = k >> 4, kk = k & 15;
+        const float b2 = p.mlp.b2[n];
+        const unsigned short hi = bf16_bits(b2);
+        const unsigned short val = kk == 0 ? hi : kk == 1 ? bf16_bits(b2 - bf16_value(hi)) : 0;
+        *reinterpret_cast<unsigned short*>(sm.bb + slice_off(n, kk)) = val;
+    }
+    if (t < 8 * 16)
+        *reinterpret_cast<unsigned short*>(sm.ones + slice_off(t >> 4, t & 15)) = (t & 15) < 2 ? 0x3F80 : 0;
+    for (int k = t; k < 2 * H; k += kMlpBlock) sm.w3[k] = p.mlp.w3[k];
     for (int k = t; k < (1 << kGridBits); k += kMlpBlock) sm.exp_tab[k] = p.exp_tab.e[k];
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.mbar)));
@@ -466,7 +527,9 @@ __global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = sm.tmem;
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(H >> 3) << 17) | ((128u >> 4) << 24);
+    // instruction descriptor: FP32 accumulators, BF16 A and B, both K-major, M = 128, N = 64
+    const uint32_t idesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(H >> 3) << 17) | ((128u >> 4) << 24);
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's TMEM lanes
     const float lo_ok = p.log_eps - (float)kWindow;
     uint32_t phase = 0;
     bool aborted = false;
@@ -498,51 +561,31 @@ __global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
                 *reinterpret_cast<uint4*>(sm.a + tile_off(t, 8 * c)) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
             }
         }
-        asm volatile("fence.proxy.async.shared::cta;");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (t == 0) {
+        sync_for_mma();
+        if (t == 0) {  // layer 2: h1 W2^T + 1 (b2 hi + b2 lo)
 #pragma unroll
-            for (int kk = 0; kk < H / 16; ++kk) {
-                const uint64_t ad = umma_desc(smem_addr(sm.a) + kk * 256, 128, 1024);
-                const uint64_t bd = umma_desc(smem_addr(sm.b) + kk * 256, 128, 1024);
-                const uint32_t acc = kk > 0;
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_addr(&sm.mbar)));
+            for (int kk = 0; kk < H / 16; ++kk)
+                mma_bf16(tmem, umma_desc(smem_addr(sm.a) + kk * 256, 128, 1024),
+                         umma_desc(smem_addr(sm.b) + kk * 256, 128, 1024), idesc2, kk > 0);
+            mma_bf16(tmem, umma_desc(smem_addr(sm.ones), 128, 0), umma_desc(smem_addr(sm.bb), 128, 256), idesc2, 1);
+            mma_commit(&sm.mbar);
         }
-        uint32_t done = 0;
-        for (int it = 0; it < kWaitLimit && !done; ++it)
-            asm volatile(
-                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                : "=r"(done)
-                : "r"(smem_addr(&sm.mbar)), "r"(phase));
-        if (__syncthreads_or(!done)) {
+        if (__syncthreads_or(!mbar_wait(&sm.mbar, phase))) {
             aborted = true;
             break;
         }
         phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // layer 2 accumulators of this thread's pair (TMEM lane t) -> layer 3
+        // layer 3 from this thread's row of the layer 2 accumulators (TMEM lane t)
         float y0 = sm.b3[0], y1 = sm.b3[1];
 #pragma unroll
         for (int c = 0; c < H; c += 16) {
             uint32_t r[16];
-            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                : "r"(addr));
+            tmem_ld16(lane_base + (uint32_t)c, r);
             asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const float h2 = fmaxf(__uint_as_float(r[j]) + sm.b2[c + j], 0.0f);
+                const float h2 = fmaxf(__uint_as_float(r[j]), 0.0f);
                 y0 = fmaf(sm.w3[c + j], h2, y0);
                 y1 = fmaf(sm.w3[H + c + j], h2, y1);
             }
@@ -605,12 +648,7 @@ __global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
                 p.fb_list[k] = (uint32_t)i;
             }
         }
-        uint32_t done = 0;  // let the MMA in flight finish before its TMEM goes (bounded)
-        for (int it = 0; it < kWaitLimit && !done; ++it)
-            asm volatile(
-                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                : "=r"(done)
-                : "r"(smem_addr(&sm.mbar)), "r"(phase));
+        mbar_wait(&sm.mbar, phase);  // let the MMA in flight finish before its TMEM goes (bounded)
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
