@@ -235,10 +235,110 @@ __device__ __forceinline__ void bin_f32(const BinsF& b, const BinsK& k, float mf
     }
 }
 
+// ------------------------------------------------------------------ two bins per instruction
+// Blackwell executes FP32 add, multiply and fused multiply-add on pairs of values (f32x2) at one
+// issue slot per pair; the bins are issue-bound, so two bins of a lane go through the same
+// arithmetic as one float2 (each component rounds exactly like the scalar instruction).
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// phi_pair for two values of s.
+__device__ __forceinline__ void phi_pair2(float2 s, float2& php, float2& phm, float2& es, float2& ems)
+{
+    const float2 sc = make_float2(fminf(fmaxf(s.x, -2.0f), 2.0f), fminf(fmaxf(s.y, -2.0f), 2.0f));
+    const float2 z = mul2(sc, sc);
+    float2 E = f2(1.0f / 87178291200.0f);  // 1/14!
+    E = fma2(E, z, f2(1.0f / 479001600.0f));
+    E = fma2(E, z, f2(1.0f / 3628800.0f));
+    E = fma2(E, z, f2(1.0f / 40320.0f));
+    E = fma2(E, z, f2(1.0f / 720.0f));
+    E = fma2(E, z, f2(1.0f / 24.0f));
+    E = fma2(E, z, f2(0.5f));
+    float2 O = f2(1.0f / 1307674368000.0f);  // 1/15!
+    O = fma2(O, z, f2(1.0f / 6227020800.0f));
+    O = fma2(O, z, f2(1.0f / 39916800.0f));
+    O = fma2(O, z, f2(1.0f / 362880.0f));
+    O = fma2(O, z, f2(1.0f / 5040.0f));
+    O = fma2(O, z, f2(1.0f / 120.0f));
+    O = fma2(O, z, f2(1.0f / 6.0f));
+    const float2 so = mul2(sc, O);
+    const float2 pp = mul2(z, add2(E, so)), pm = mul2(z, sub2(E, so));
+    const float2 eb = make_float2(expf(s.x), expf(s.y));
+    const float2 ebi = make_float2(rcp_approx(eb.x), rcp_approx(eb.y));
+    const float2 bp = sub2(add2(eb, f2(-1.0f)), s), bm = add2(add2(ebi, f2(-1.0f)), s);
+    const float2 sp = add2(add2(f2(1.0f), sc), pp), sm = add2(sub2(f2(1.0f), sc), pm);
+    const bool kx = fabsf(s.x) <= 2.0f, ky = fabsf(s.y) <= 2.0f;
+    php = make_float2(kx ? pp.x : bp.x, ky ? pp.y : bp.y);
+    phm = make_float2(kx ? pm.x : bm.x, ky ? pm.y : bm.y);
+    es = make_float2(kx ? sp.x : eb.x, ky ? sp.y : eb.y);
+    ems = make_float2(kx ? sm.x : ebi.x, ky ? sm.y : ebi.y);
+}
+
+__device__ __forceinline__ float2 tanh_small2(float2 y)
+{
+    const float2 z = mul2(y, y);
+    float2 p = f2(-443861162.0f / 1856156927625.0f);
+    p = fma2(p, z, f2(6404582.0f / 10854718875.0f));
+    p = fma2(p, z, f2(-929569.0f / 638512875.0f));
+    p = fma2(p, z, f2(21844.0f / 6081075.0f));
+    p = fma2(p, z, f2(-1382.0f / 155925.0f));
+    p = fma2(p, z, f2(62.0f / 2835.0f));
+    p = fma2(p, z, f2(-17.0f / 315.0f));
+    p = fma2(p, z, f2(2.0f / 15.0f));
+    p = fma2(p, z, f2(-1.0f / 3.0f));
+    return fma2(mul2(y, z), p, y);
+}
+
+// bin_f32 for the two bins m = mf.x and mf.y; c0 is the weight factor of the first of them.
+template <bool DERIV, bool VOTE>
+__device__ __forceinline__ void bin_f32x2(const BinsF& b, const BinsK& k, float2 mf, float c0, float2& w,
+                                          float2& w1, float2& w2)
+{
+    const float2 s = fma2(mf, f2(b.h), f2(b.s0));
+    float2 php, phm, es, ems;
+    phi_pair2(s, php, phm, es, ems);
+    const float2 vt = fma2(f2(b.v), s, f2(b.u));
+    const float2 ea = mul2(vt, f2(-2.0f * LOG2E_F));
+    const float2 e2 = make_float2(ex2_approx(ea.x), ex2_approx(ea.y));  // e^{-2vt}
+    const float2 ope = add2(f2(1.0f), e2);
+    const float2 d = sub2(make_float2(lg2_approx(ope.x), lg2_approx(ope.y)), f2(k.lu));
+    const float2 dg = sub2(fma2(f2(k.c1), s, d), fma2(f2(k.ap), php, mul2(f2(k.am), phm)));
+    w = make_float2(c0 * ex2_approx(dg.x), ex2_approx(dg.y));
+    if (DERIV) {
+        const float2 t = add2(f2(b.tp), s);
+        float2 th = mul2(sub2(f2(1.0f), e2), make_float2(rcp_approx(ope.x), rcp_approx(ope.y)));  // tanh(vt)
+        const bool kx = vt.x < TANH_SERIES_MAX, ky = vt.y < TANH_SERIES_MAX;
+        if (!VOTE || __any_sync(0xffffffffu, kx || ky)) {
+            const float2 ts = tanh_small2(vt);
+            th = make_float2(kx ? ts.x : th.x, ky ? ts.y : th.y);
+        }
+        w1 = mul2(w, mul2(t, th));
+        w2 = mul2(w, fma2(f2(k.hep), es, mul2(f2(k.hem), ems)));  // w cosh t
+    }
+}
+
+// Kahan accumulation of two running sums at once.
+struct KahanSum2 {
+    float2 s, c;
+    __device__ __forceinline__ void init() { s = c = f2(0.0f); }
+    __device__ __forceinline__ void add(float2 w)
+    {
+        const float2 y = sub2(w, c);
+        const float2 t = add2(s, y);
+        c = sub2(sub2(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return (s.x - c.x) + (s.y - c.y); }
+};
+
 // The three sums over bins m = lane, lane + L, ... <= n, compensated per block of four bins: a
-// block's four terms are added pairwise (two rounding levels) and the block sum goes into a Kahan
-// sum, so the relative error stays a few units of 2^-24 for any bin count at 1.75 additions per
-// term instead of Kahan's four.  The end weight 1/2 of bin 0 is applied to the first block's
+// block's four terms are added in pairs and the two pair sums go into a two-lane Kahan sum, so
+// the relative error stays a few units of 2^-24 for any bin count at 1.25 paired additions per
+// two terms.  The end weight 1/2 of bin 0 is applied to the first block's
 // first term (lane 0 only); bin n always falls in the tail loop, which selects its weight.
 // VOTE requires L = 1 and all 32 lanes of the warp in the call with the same n.
 template <int L, bool DERIV, bool VOTE = false>
@@ -246,25 +346,31 @@ __device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, fl
 {
     static_assert(!VOTE || L == 1, "the warp vote needs every lane on the same bins");
     const BinsK k = bins_k(b);
-    KahanSum<float> k0, k1, k2;
-    k0.init();
-    k1.init();
-    k2.init();
+    KahanSum2 q0, q1, q2;
+    q0.init();
+    q1.init();
+    q2.init();
     int m = lane;
     float mf = (float)lane;
     float c_first = lane == 0 ? 0.5f : 1.0f;
     for (; m + 3 * L < b.n; m += 4 * L, mf += (float)(4 * L)) {
-        float w[4], w1[4], w2[4];
-        bin_f32<DERIV, VOTE>(b, k, mf, c_first, w[0], w1[0], w2[0]);
-#pragma unroll
-        for (int q = 1; q < 4; ++q) bin_f32<DERIV, VOTE>(b, k, mf + (float)(q * L), 1.0f, w[q], w1[q], w2[q]);
+        // bins m, m + L in one float2 and m + 2L, m + 3L in another; the block's four terms are
+        // added pairwise, (w_m + w_{m+2L}) and (w_{m+L} + w_{m+3L}) into the two Kahan lanes
+        float2 wa, w1a, w2a, wb, w1b, w2b;
+        bin_f32x2<DERIV, VOTE>(b, k, make_float2(mf, mf + (float)L), c_first, wa, w1a, w2a);
+        bin_f32x2<DERIV, VOTE>(b, k, make_float2(mf + (float)(2 * L), mf + (float)(3 * L)), 1.0f, wb, w1b, w2b);
         c_first = 1.0f;
-        k0.add((w[0] + w[1]) + (w[2] + w[3]));
+        q0.add(add2(wa, wb));
         if (DERIV) {
-            k1.add((w1[0] + w1[1]) + (w1[2] + w1[3]));
-            k2.add((w2[0] + w2[1]) + (w2[2] + w2[3]));
+            q1.add(add2(w1a, w1b));
+            q2.add(add2(w2a, w2b));
         }
     }
+    KahanSum<float> k0, k1, k2;
+    k0.s = q0.value();
+    k1.s = q1.value();
+    k2.s = q2.value();
+    k0.c = k1.c = k2.c = 0.0f;
     for (; m <= b.n; m += L, mf += (float)L) {
         float w, w1, w2;
         bin_f32<DERIV, VOTE>(b, k, mf, (m == 0 || m == b.n) ? 0.5f : 1.0f, w, w1, w2);
