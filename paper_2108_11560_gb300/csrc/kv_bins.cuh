@@ -112,35 +112,51 @@ struct BinsF {
     int n;
 };
 
-// phi(s) = e^s - 1 - s and phi(-s), and e^{+-s}, each to a few FP32 ulps relative.
-// |s| <= 2: even/odd Taylor parts of phi in z = s^2 (terms to s^15; the rest < 2e-9 relative).
-// |s| > 2: from expf (no cancellation there: phi(2) = 4.39, phi(-2) = 1.14).
-// Both forms are computed (the series on s clamped to [-2, 2]) and the valid one is selected:
-// lanes of a warp whose bins straddle |s| = 2 would otherwise run both sides one after the other.
+// Blackwell executes FP32 add, multiply and fused multiply-add on pairs of values (f32x2) at one
+// issue slot per pair; the bins were issue-bound, so two bins of a lane go through the same
+// arithmetic as one float2 (each component rounds exactly like the scalar instruction).
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// phi(s) = e^s - 1 - s and phi(-s), and e^{+-s}.
+// |s| <= 1: even/odd Taylor parts of phi in z = s^2 (terms to s^12 and s^11; the rest is below
+// 3e-10 relative), a few FP32 ulps relative.
+// |s| > 1: from expf, where the cancellation in e^s - 1 - s costs at most one ulp of e (phi(1) =
+// 0.718, phi(-1) = 0.368: relative error below 6e-7 at |s| = 1, falling fast beyond).  The
+// weight of such a bin is exp(-(x e^{t_p}/2) phi(s) - ...), so the absolute error this leaves in
+// its exponent stays below 3e-7 wherever the bin's weight is not negligible.
+// Both forms are computed (the series on s clamped to [-1, 1]) and the valid one is selected:
+// lanes of a warp whose bins straddle |s| = 1 would otherwise run both sides one after the other.
+constexpr float PHI_SERIES_MAX = 1.0f;
+
+// E(z) = sum_{k>=1} z^{k-1}/(2k)!,  O(z) = sum_{k>=1} z^{k-1}/(2k+1)!  for z <= 1
+#define KV_PHI_SERIES(MUL, FMA, C, z, E, O)                 \
+    E = FMA(C(1.0f / 479001600.0f), z, C(1.0f / 3628800.0f)); \
+    E = FMA(E, z, C(1.0f / 40320.0f));                        \
+    E = FMA(E, z, C(1.0f / 720.0f));                          \
+    E = FMA(E, z, C(1.0f / 24.0f));                           \
+    E = FMA(E, z, C(0.5f));                                   \
+    O = FMA(C(1.0f / 39916800.0f), z, C(1.0f / 362880.0f));   \
+    O = FMA(O, z, C(1.0f / 5040.0f));                         \
+    O = FMA(O, z, C(1.0f / 120.0f));                          \
+    O = FMA(O, z, C(1.0f / 6.0f));
+
+__device__ __forceinline__ float f1(float a) { return a; }
+
 __device__ __forceinline__ void phi_pair(float s, float& php, float& phm, float& es, float& ems)
 {
-    const float sc = fminf(fmaxf(s, -2.0f), 2.0f);
+    const float sc = fminf(fmaxf(s, -PHI_SERIES_MAX), PHI_SERIES_MAX);
     const float z = sc * sc;
-    // E(z) = sum_{k>=1} z^{k-1}/(2k)!,  O(z) = sum_{k>=1} z^{k-1}/(2k+1)!
-    float E = 1.0f / 87178291200.0f;  // 1/14!
-    E = fmaf(E, z, 1.0f / 479001600.0f);
-    E = fmaf(E, z, 1.0f / 3628800.0f);
-    E = fmaf(E, z, 1.0f / 40320.0f);
-    E = fmaf(E, z, 1.0f / 720.0f);
-    E = fmaf(E, z, 1.0f / 24.0f);
-    E = fmaf(E, z, 0.5f);
-    float O = 1.0f / 1307674368000.0f;  // 1/15!
-    O = fmaf(O, z, 1.0f / 6227020800.0f);
-    O = fmaf(O, z, 1.0f / 39916800.0f);
-    O = fmaf(O, z, 1.0f / 362880.0f);
-    O = fmaf(O, z, 1.0f / 5040.0f);
-    O = fmaf(O, z, 1.0f / 120.0f);
-    O = fmaf(O, z, 1.0f / 6.0f);
+    float E, O;
+    KV_PHI_SERIES(__fmul_rn, fmaf, f1, z, E, O)
     const float so = sc * O;
     const float pp = z * (E + so), pm = z * (E - so);
     const float eb = expf(s);
     const float ebi = rcp_approx(eb);
-    const bool small = fabsf(s) <= 2.0f;
+    const bool small = fabsf(s) <= PHI_SERIES_MAX;
     php = small ? pp : (eb - 1.0f) - s;
     phm = small ? pm : (ebi - 1.0f) + s;
     es = small ? (1.0f + sc) + pp : eb;
@@ -236,42 +252,22 @@ __device__ __forceinline__ void bin_f32(const BinsF& b, const BinsK& k, float mf
 }
 
 // ------------------------------------------------------------------ two bins per instruction
-// Blackwell executes FP32 add, multiply and fused multiply-add on pairs of values (f32x2) at one
-// issue slot per pair; the bins are issue-bound, so two bins of a lane go through the same
-// arithmetic as one float2 (each component rounds exactly like the scalar instruction).
-
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // phi_pair for two values of s.
 __device__ __forceinline__ void phi_pair2(float2 s, float2& php, float2& phm, float2& es, float2& ems)
 {
-    const float2 sc = make_float2(fminf(fmaxf(s.x, -2.0f), 2.0f), fminf(fmaxf(s.y, -2.0f), 2.0f));
+    const float2 sc = make_float2(fminf(fmaxf(s.x, -PHI_SERIES_MAX), PHI_SERIES_MAX),
+                                  fminf(fmaxf(s.y, -PHI_SERIES_MAX), PHI_SERIES_MAX));
     const float2 z = mul2(sc, sc);
-    float2 E = f2(1.0f / 87178291200.0f);  // 1/14!
-    E = fma2(E, z, f2(1.0f / 479001600.0f));
-    E = fma2(E, z, f2(1.0f / 3628800.0f));
-    E = fma2(E, z, f2(1.0f / 40320.0f));
-    E = fma2(E, z, f2(1.0f / 720.0f));
-    E = fma2(E, z, f2(1.0f / 24.0f));
-    E = fma2(E, z, f2(0.5f));
-    float2 O = f2(1.0f / 1307674368000.0f);  // 1/15!
-    O = fma2(O, z, f2(1.0f / 6227020800.0f));
-    O = fma2(O, z, f2(1.0f / 39916800.0f));
-    O = fma2(O, z, f2(1.0f / 362880.0f));
-    O = fma2(O, z, f2(1.0f / 5040.0f));
-    O = fma2(O, z, f2(1.0f / 120.0f));
-    O = fma2(O, z, f2(1.0f / 6.0f));
+    float2 E, O;
+    KV_PHI_SERIES(mul2, fma2, f2, z, E, O)
     const float2 so = mul2(sc, O);
     const float2 pp = mul2(z, add2(E, so)), pm = mul2(z, sub2(E, so));
     const float2 eb = make_float2(expf(s.x), expf(s.y));
     const float2 ebi = make_float2(rcp_approx(eb.x), rcp_approx(eb.y));
     const float2 bp = sub2(add2(eb, f2(-1.0f)), s), bm = add2(add2(ebi, f2(-1.0f)), s);
     const float2 sp = add2(add2(f2(1.0f), sc), pp), sm = add2(sub2(f2(1.0f), sc), pm);
-    const bool kx = fabsf(s.x) <= 2.0f, ky = fabsf(s.y) <= 2.0f;
+    const bool kx = fabsf(s.x) <= PHI_SERIES_MAX, ky = fabsf(s.y) <= PHI_SERIES_MAX;
     php = make_float2(kx ? pp.x : bp.x, ky ? pp.y : bp.y);
     phm = make_float2(kx ? pm.x : bm.x, ky ? pm.y : bm.y);
     es = make_float2(kx ? sp.x : eb.x, ky ? sp.y : eb.y);
@@ -321,24 +317,10 @@ __device__ __forceinline__ void bin_f32x2(const BinsF& b, const BinsK& k, float2
     }
 }
 
-// Kahan accumulation of two running sums at once.
-struct KahanSum2 {
-    float2 s, c;
-    __device__ __forceinline__ void init() { s = c = f2(0.0f); }
-    __device__ __forceinline__ void add(float2 w)
-    {
-        const float2 y = sub2(w, c);
-        const float2 t = add2(s, y);
-        c = sub2(sub2(t, s), y);
-        s = t;
-    }
-    __device__ __forceinline__ float value() const { return (s.x - c.x) + (s.y - c.y); }
-};
-
 // The three sums over bins m = lane, lane + L, ... <= n, compensated per block of four bins: a
-// block's four terms are added in pairs and the two pair sums go into a two-lane Kahan sum, so
-// the relative error stays a few units of 2^-24 for any bin count at 1.25 paired additions per
-// two terms.  The end weight 1/2 of bin 0 is applied to the first block's
+// block's four terms are added pairwise (two rounding levels) and the block sum goes into a Kahan
+// sum, so the relative error stays a few units of 2^-24 for any bin count at 1.75 additions per
+// term instead of Kahan's four.  The end weight 1/2 of bin 0 is applied to the first block's
 // first term (lane 0 only); bin n always falls in the tail loop, which selects its weight.
 // VOTE requires L = 1 and all 32 lanes of the warp in the call with the same n.
 template <int L, bool DERIV, bool VOTE = false>
@@ -346,31 +328,28 @@ __device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, fl
 {
     static_assert(!VOTE || L == 1, "the warp vote needs every lane on the same bins");
     const BinsK k = bins_k(b);
-    KahanSum2 q0, q1, q2;
-    q0.init();
-    q1.init();
-    q2.init();
+    KahanSum<float> k0, k1, k2;
+    k0.init();
+    k1.init();
+    k2.init();
     int m = lane;
     float mf = (float)lane;
     float c_first = lane == 0 ? 0.5f : 1.0f;
     for (; m + 3 * L < b.n; m += 4 * L, mf += (float)(4 * L)) {
         // bins m, m + L in one float2 and m + 2L, m + 3L in another; the block's four terms are
-        // added pairwise, (w_m + w_{m+2L}) and (w_{m+L} + w_{m+3L}) into the two Kahan lanes
+        // added pairwise, (w_m + w_{m+2L}) + (w_{m+L} + w_{m+3L}), and the sum goes to Kahan
         float2 wa, w1a, w2a, wb, w1b, w2b;
         bin_f32x2<DERIV, VOTE>(b, k, make_float2(mf, mf + (float)L), c_first, wa, w1a, w2a);
         bin_f32x2<DERIV, VOTE>(b, k, make_float2(mf + (float)(2 * L), mf + (float)(3 * L)), 1.0f, wb, w1b, w2b);
         c_first = 1.0f;
-        q0.add(add2(wa, wb));
+        const float2 p0 = add2(wa, wb);
+        k0.add(p0.x + p0.y);
         if (DERIV) {
-            q1.add(add2(w1a, w1b));
-            q2.add(add2(w2a, w2b));
+            const float2 p1 = add2(w1a, w1b), p2 = add2(w2a, w2b);
+            k1.add(p1.x + p1.y);
+            k2.add(p2.x + p2.y);
         }
     }
-    KahanSum<float> k0, k1, k2;
-    k0.s = q0.value();
-    k1.s = q1.value();
-    k2.s = q2.value();
-    k0.c = k1.c = k2.c = 0.0f;
     for (; m <= b.n; m += L, mf += (float)L) {
         float w, w1, w2;
         bin_f32<DERIV, VOTE>(b, k, mf, (m == 0 || m == b.n) ? 0.5f : 1.0f, w, w1, w2);

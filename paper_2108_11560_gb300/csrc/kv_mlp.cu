@@ -421,7 +421,9 @@ struct TcSmem {
     unsigned char b[H * H * 2];      // W2 (BF16): row = output unit, K = input unit
     unsigned char bb[H * 16 * 2];    // B of layer 2's extra K slice: k = 0, 1 hold b2 split hi + lo
     unsigned char ones[8 * 16 * 2];  // A of that slice, one 8-row group read by every group: 1, 1, 0...
-    float w1[2 * H], b1[H], w3[2 * H], b3[2];
+    float2 w1a[H / 2], w1b[H / 2], b1[H / 2];  // layer 1 by unit pairs: {W1[u][0], W1[u+1][0]}, ...
+    float2 w3[H];                              // {W3[0][j], W3[1][j]}
+    float b3[2];
     float in_scale[4], out_scale[4];
     float4 exp_tab[1 << kGridBits];
     uint64_t mbar;
@@ -489,13 +491,17 @@ constexpr uint32_t kTmemCols = 64;
 // than the 128 FMAs it saves.)  A wait that does not finish within its limit sends the CTA's
 // remaining pairs to the fallback list (correct, slower) instead of hanging.
 template <bool DERIV>
-__global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
+__global__ void __launch_bounds__(kMlpBlock, 7) kv_mlp_tc_kernel(MlpPathParams p)
 {
     __shared__ __align__(1024) TcSmem sm;
     const int t = threadIdx.x;
     const int warp = t >> 5;
-    for (int k = t; k < 2 * H; k += kMlpBlock) sm.w1[k] = p.mlp.w1[k];
-    for (int k = t; k < H; k += kMlpBlock) sm.b1[k] = p.mlp.b1[k];
+    for (int k = t; k < H / 2; k += kMlpBlock) {
+        sm.w1a[k] = make_float2(p.mlp.w1[4 * k], p.mlp.w1[4 * k + 2]);
+        sm.w1b[k] = make_float2(p.mlp.w1[4 * k + 1], p.mlp.w1[4 * k + 3]);
+        sm.b1[k] = make_float2(p.mlp.b1[2 * k], p.mlp.b1[2 * k + 1]);
+    }
+    for (int k = t; k < H; k += kMlpBlock) sm.w3[k] = make_float2(p.mlp.w3[k], p.mlp.w3[H + k]);
     if (t < 2) sm.b3[t] = p.mlp.b3[t];
     if (t < 4) {
         sm.in_scale[t] = p.mlp.in_scale[t];
@@ -512,7 +518,6 @@ __global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
     }
     if (t < 8 * 16)
         *reinterpret_cast<unsigned short*>(sm.ones + slice_off(t >> 4, t & 15)) = (t & 15) < 2 ? 0x3F80 : 0;
-    for (int k = t; k < 2 * H; k += kMlpBlock) sm.w3[k] = p.mlp.w3[k];
     for (int k = t; k < (1 << kGridBits); k += kMlpBlock) sm.exp_tab[k] = p.exp_tab.e[k];
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.mbar)));
@@ -552,11 +557,10 @@ __global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
                 uint32_t packed[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int u0 = 8 * c + 2 * q, u1 = u0 + 1;
-                    const float z0 = fmaf(sm.w1[2 * u0], a, fmaf(sm.w1[2 * u0 + 1], b, sm.b1[u0]));
-                    const float z1 = fmaf(sm.w1[2 * u1], a, fmaf(sm.w1[2 * u1 + 1], b, sm.b1[u1]));
-                    // relu and round to BF16 in one conversion (unit u0 in the low half)
-                    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(packed[q]) : "f"(z1), "f"(z0));
+                    const int u = 4 * c + q;  // units 2u, 2u + 1
+                    const float2 z = fma2(sm.w1a[u], f2(a), fma2(sm.w1b[u], f2(b), sm.b1[u]));
+                    // relu and round to BF16 in one conversion (unit 2u in the low half)
+                    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(packed[q]) : "f"(z.y), "f"(z.x));
                 }
                 *reinterpret_cast<uint4*>(sm.a + tile_off(t, 8 * c)) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
             }
@@ -577,19 +581,16 @@ __global__ void __launch_bounds__(kMlpBlock) kv_mlp_tc_kernel(MlpPathParams p)
         phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;");
         // layer 3 from this thread's row of the layer 2 accumulators (TMEM lane t)
-        float y0 = sm.b3[0], y1 = sm.b3[1];
+        float2 y = make_float2(sm.b3[0], sm.b3[1]);
 #pragma unroll
         for (int c = 0; c < H; c += 16) {
             uint32_t r[16];
             tmem_ld16(lane_base + (uint32_t)c, r);
             asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float h2 = fmaxf(__uint_as_float(r[j]), 0.0f);
-                y0 = fmaf(sm.w3[c + j], h2, y0);
-                y1 = fmaf(sm.w3[H + c + j], h2, y1);
-            }
+            for (int j = 0; j < 16; ++j) y = fma2(sm.w3[c + j], f2(fmaxf(__uint_as_float(r[j]), 0.0f)), y);
         }
+        const float y0 = y.x, y1 = y.y;
         asm volatile("tcgen05.fence::before_thread_sync;");
         // Every lane runs the same straight-line code from here (edge and inactive lanes on
         // their placeholder inputs), so the warp is converged when it enters the bins:
