@@ -124,10 +124,11 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // phi(s) = e^s - 1 - s and phi(-s), and e^{+-s}.
 // |s| <= 1: even/odd Taylor parts of phi in z = s^2 (terms to s^12 and s^11; the rest is below
 // 3e-10 relative), a few FP32 ulps relative.
-// |s| > 1: from expf, where the cancellation in e^s - 1 - s costs at most one ulp of e (phi(1) =
-// 0.718, phi(-1) = 0.368: relative error below 6e-7 at |s| = 1, falling fast beyond).  The
+// |s| > 1: from e^s = 2^{s log2 e} (ex2.approx: relative error about 2^-22 plus the rounding of
+// s log2 e, |s| 2^-24 relative), where the cancellation in e^s - 1 - s costs at most a few ulps of
+// e (phi(1) = 0.718, phi(-1) = 0.368: relative error below 1e-6 at |s| = 1, falling beyond).  The
 // weight of such a bin is exp(-(x e^{t_p}/2) phi(s) - ...), so the absolute error this leaves in
-// its exponent stays below 3e-7 wherever the bin's weight is not negligible.
+// its exponent stays below 1e-6 wherever the bin's weight is not negligible.
 // Both forms are computed (the series on s clamped to [-1, 1]) and the valid one is selected:
 // lanes of a warp whose bins straddle |s| = 1 would otherwise run both sides one after the other.
 constexpr float PHI_SERIES_MAX = 1.0f;
@@ -154,7 +155,7 @@ __device__ __forceinline__ void phi_pair(float s, float& php, float& phm, float&
     KV_PHI_SERIES(__fmul_rn, fmaf, f1, z, E, O)
     const float so = sc * O;
     const float pp = z * (E + so), pm = z * (E - so);
-    const float eb = expf(s);
+    const float eb = ex2_approx(s * LOG2E_F);
     const float ebi = rcp_approx(eb);
     const bool small = fabsf(s) <= PHI_SERIES_MAX;
     php = small ? pp : (eb - 1.0f) - s;
@@ -163,15 +164,13 @@ __device__ __forceinline__ void phi_pair(float s, float& php, float& phm, float&
     ems = small ? (1.0f - sc) + pm : ebi;
 }
 
-// tanh(y) for |y| < 0.625 by its Taylor series through y^19 (relative error < 1e-8 there);
-// (1 - e^{-2y}) / (1 + e^{-2y}) loses relative precision to the cancellation in 1 - e^{-2y}.
+// tanh(y) for |y| < 0.35 by its Taylor series through y^13 (relative error < 1e-9 there);
+// (1 - e^{-2y}) / (1 + e^{-2y}) loses relative precision to the cancellation in 1 - e^{-2y}
+// (about 2^-22 / (2y) relative: below 4e-7 from y = 0.35 on).
 __device__ __forceinline__ float tanh_small(float y)
 {
     float z = y * y;
-    float p = -443861162.0f / 1856156927625.0f;
-    p = fmaf(p, z, 6404582.0f / 10854718875.0f);
-    p = fmaf(p, z, -929569.0f / 638512875.0f);
-    p = fmaf(p, z, 21844.0f / 6081075.0f);
+    float p = 21844.0f / 6081075.0f;
     p = fmaf(p, z, -1382.0f / 155925.0f);
     p = fmaf(p, z, 62.0f / 2835.0f);
     p = fmaf(p, z, -17.0f / 315.0f);
@@ -223,7 +222,7 @@ __device__ __forceinline__ BinsK bins_k(const BinsF& b)
 }
 
 // vt below this uses tanh_small
-constexpr float TANH_SERIES_MAX = 0.625f;
+constexpr float TANH_SERIES_MAX = 0.35f;
 
 // One FP32 bin at m = mf (a float holding a small integer, exact): its weight c e^{g(t_m) - g(t_p)}
 // and the two derivative integrands' weights.  With VOTE (all 32 lanes of the warp run the same
@@ -263,7 +262,8 @@ __device__ __forceinline__ void phi_pair2(float2 s, float2& php, float2& phm, fl
     KV_PHI_SERIES(mul2, fma2, f2, z, E, O)
     const float2 so = mul2(sc, O);
     const float2 pp = mul2(z, add2(E, so)), pm = mul2(z, sub2(E, so));
-    const float2 eb = make_float2(expf(s.x), expf(s.y));
+    const float2 el = mul2(s, f2(LOG2E_F));
+    const float2 eb = make_float2(ex2_approx(el.x), ex2_approx(el.y));
     const float2 ebi = make_float2(rcp_approx(eb.x), rcp_approx(eb.y));
     const float2 bp = sub2(add2(eb, f2(-1.0f)), s), bm = add2(add2(ebi, f2(-1.0f)), s);
     const float2 sp = add2(add2(f2(1.0f), sc), pp), sm = add2(sub2(f2(1.0f), sc), pm);
@@ -277,10 +277,7 @@ __device__ __forceinline__ void phi_pair2(float2 s, float2& php, float2& phm, fl
 __device__ __forceinline__ float2 tanh_small2(float2 y)
 {
     const float2 z = mul2(y, y);
-    float2 p = f2(-443861162.0f / 1856156927625.0f);
-    p = fma2(p, z, f2(6404582.0f / 10854718875.0f));
-    p = fma2(p, z, f2(-929569.0f / 638512875.0f));
-    p = fma2(p, z, f2(21844.0f / 6081075.0f));
+    float2 p = f2(21844.0f / 6081075.0f);
     p = fma2(p, z, f2(-1382.0f / 155925.0f));
     p = fma2(p, z, f2(62.0f / 2835.0f));
     p = fma2(p, z, f2(-17.0f / 315.0f));

@@ -8,7 +8,7 @@
 //   L_k = y_k * out[2k] + out[2k+1];  t0 = max(t_ref - max(e^{L_0} - DELTA, 0), 0),
 //   t1 = t_ref + max(e^{L_1} - DELTA, 0), with t_ref the peak of g.
 // The network predicts log half-widths of the range about the peak; the peak itself comes from
-// four FP32 Newton steps on g' from asinh(v/x) (g' is concave and <= 0 there, so the iterates
+// three FP32 Newton steps on g' from asinh(v/x) (g' is concave and <= 0 there, so the iterates
 // fall monotonically onto the zero).
 //
 // Fast path per pair (kv_mlp_tc_kernel): MLP (hidden layer on the tensor cores) -> peak ->
@@ -145,16 +145,19 @@ __device__ __forceinline__ float fast_asinh(float z)
     return __logf(fmaf(q, r, z));
 }
 
-// The peak of g by four FP32 Newton steps from asinh(v/x) (0 when v^2 <= x).  Its accuracy does
-// not enter the results (the bins are exact relative to any reference point near the peak), so
-// the steps use the approximate exponential, reciprocal and division.  The start is nudged up so
-// that it stays on the side of the zero where g' <= 0 despite the approximate asinh.
+// The peak of g by STEPS FP32 Newton steps from asinh(v/x) (0 when v^2 <= x).  On the fast path
+// (three steps) its accuracy does not enter the results (the bins are exact relative to any
+// reference point near the peak); the training targets and the raw predictions, which are
+// measured from the peak, take eight.  The steps use the approximate exponential, reciprocal and
+// division.  The start is nudged up so that it stays on the side of the zero where g' <= 0
+// despite the approximate asinh.
+template <int STEPS = 3>
 __device__ __forceinline__ float peak_f32(float v, float x)
 {
     if (!(v * v > x)) return 0.0f;
     float t = fast_asinh(__fdividef(v, x)) * (1.0f + 0x1.0p-16f);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < STEPS; ++k) {
         float e2 = ex2_approx(-2.0f * LOG2E_F * v * t);
         float r = rcp_approx(1.0f + e2);
         float th = (1.0f - e2) * r;
@@ -278,7 +281,8 @@ __device__ __forceinline__ PeakConst peak_constants(float v, float x, float tp, 
     tr = fast_two_sum(tr.hi, fmaf(j, kGridStepLo, tr.lo));
     df u = two_prod(v, tr.hi);
     u = fast_two_sum(u.hi, fmaf(v, tr.lo, u.lo));
-    const float lu = log1pf(expf(-2.0f * u.hi));
+    // log1p(e^{-2u}) in [0, ln 2] from the approximate 2^x and log2 (absolute error ~2e-7)
+    const float lu = lg2_approx(1.0f + ex2_approx(-2.0f * LOG2E_F * u.hi)) * LN2_F;
     const df ch = df_mul_f(df_add_fast(E, Ei), 0.5f * x);  // x cosh t_r
     const df sh = df_mul_f(df_sub_fast(E, Ei), 0.5f * x);  // x sinh t_r
     c.G = df_sub_fast(df_add_fast(df_add_fast(u, df_make(lu)), df_neg(df_ln2())), ch);
@@ -761,7 +765,7 @@ __global__ void __launch_bounds__(kMlpBlock) kv_predict_kernel(kvh::MlpView m, c
         const float va = fabsf(v[i]);
         float L0, L1;
         mlp_forward(sm, va, x[i], L0, L1);
-        const float tr = peak_f32(va, x[i]);
+        const float tr = peak_f32<8>(va, x[i]);
         t0[i] = fmaxf(tr - fmaxf(__expf(L0) - DELTA, 0.0f), 0.0f);
         t1[i] = tr + fmaxf(__expf(L1) - DELTA, 0.0f);
     }
@@ -832,7 +836,7 @@ __global__ void __launch_bounds__(kTrainBlock) mlp_grad_kernel(GradArgs g)
             y1 = fmaf(W[OFF_W3 + H + j], z, y1);
         }
         // targets: log half-widths about the peak
-        const float tr = peak_f32((float)vd, (float)xd);
+        const float tr = peak_f32<8>((float)vd, (float)xd);
         const double T0 = (log(fmax((double)tr - g.t0[idx], 0.0) + (double)DELTA) - g.out_scale[1]) / g.out_scale[0];
         const double T1 = (log(fmax(g.t1[idx] - (double)tr, 0.0) + (double)DELTA) - g.out_scale[3]) / g.out_scale[2];
         const float r0 = y0 - (float)T0, r1 = y1 - (float)T1;
