@@ -129,8 +129,11 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // e (phi(1) = 0.718, phi(-1) = 0.368: relative error below 1e-6 at |s| = 1, falling beyond).  The
 // weight of such a bin is exp(-(x e^{t_p}/2) phi(s) - ...), so the absolute error this leaves in
 // its exponent stays below 1e-6 wherever the bin's weight is not negligible.
-// Both forms are computed (the series on s clamped to [-1, 1]) and the valid one is selected:
-// lanes of a warp whose bins straddle |s| = 1 would otherwise run both sides one after the other.
+// Both forms are computed and the valid one is selected: lanes of a warp whose bins straddle
+// |s| = 1 would otherwise run both sides one after the other.  (The series at |s| > 1 is
+// discarded; it stays finite far beyond any range the bins cover, and an overflow there would
+// not reach the selected value.)  e^{+-s} themselves (for cosh t in the d/dx integrand, which
+// needs only FP32 relative accuracy) always come from ex2 and its reciprocal.
 constexpr float PHI_SERIES_MAX = 1.0f;
 
 // E(z) = sum_{k>=1} z^{k-1}/(2k)!,  O(z) = sum_{k>=1} z^{k-1}/(2k+1)!  for z <= 1
@@ -149,19 +152,16 @@ __device__ __forceinline__ float f1(float a) { return a; }
 
 __device__ __forceinline__ void phi_pair(float s, float& php, float& phm, float& es, float& ems)
 {
-    const float sc = fminf(fmaxf(s, -PHI_SERIES_MAX), PHI_SERIES_MAX);
-    const float z = sc * sc;
+    const float z = s * s;
     float E, O;
     KV_PHI_SERIES(__fmul_rn, fmaf, f1, z, E, O)
-    const float so = sc * O;
+    const float so = s * O;
     const float pp = z * (E + so), pm = z * (E - so);
-    const float eb = ex2_approx(s * LOG2E_F);
-    const float ebi = rcp_approx(eb);
+    es = ex2_approx(s * LOG2E_F);
+    ems = rcp_approx(es);
     const bool small = fabsf(s) <= PHI_SERIES_MAX;
-    php = small ? pp : (eb - 1.0f) - s;
-    phm = small ? pm : (ebi - 1.0f) + s;
-    es = small ? (1.0f + sc) + pp : eb;
-    ems = small ? (1.0f - sc) + pm : ebi;
+    php = small ? pp : (es - 1.0f) - s;
+    phm = small ? pm : (ems - 1.0f) + s;
 }
 
 // tanh(y) for |y| < 0.35 by its Taylor series through y^13 (relative error < 1e-9 there);
@@ -235,9 +235,9 @@ __device__ __forceinline__ void bin_f32(const BinsF& b, const BinsK& k, float mf
     float php, phm, es, ems;
     phi_pair(s, php, phm, es, ems);
     const float vt = fmaf(b.v, s, b.u);
-    const float e2 = ex2_approx(-2.0f * LOG2E_F * vt);     // e^{-2vt}
-    const float d = lg2_approx(1.0f + e2) - k.lu;          // [log1p(e^{-2vt}) - log1p(e^{-2u})] log2 e
-    const float dg = fmaf(k.c1, s, d) - fmaf(k.ap, php, k.am * phm);
+    const float e2 = ex2_approx(-2.0f * LOG2E_F * vt);  // e^{-2vt}
+    // (g(t) - g(t_p)) log2 e with log1p(e^{-2vt}) - log1p(e^{-2u}) as lg2(1 + e2) - lu
+    const float dg = fmaf(k.c1, s, lg2_approx(1.0f + e2)) - fmaf(k.ap, php, fmaf(k.am, phm, k.lu));
     w = c * ex2_approx(dg);
     if (DERIV) {
         const float t = b.tp + s;
@@ -255,23 +255,18 @@ __device__ __forceinline__ void bin_f32(const BinsF& b, const BinsK& k, float mf
 // phi_pair for two values of s.
 __device__ __forceinline__ void phi_pair2(float2 s, float2& php, float2& phm, float2& es, float2& ems)
 {
-    const float2 sc = make_float2(fminf(fmaxf(s.x, -PHI_SERIES_MAX), PHI_SERIES_MAX),
-                                  fminf(fmaxf(s.y, -PHI_SERIES_MAX), PHI_SERIES_MAX));
-    const float2 z = mul2(sc, sc);
+    const float2 z = mul2(s, s);
     float2 E, O;
     KV_PHI_SERIES(mul2, fma2, f2, z, E, O)
-    const float2 so = mul2(sc, O);
+    const float2 so = mul2(s, O);
     const float2 pp = mul2(z, add2(E, so)), pm = mul2(z, sub2(E, so));
     const float2 el = mul2(s, f2(LOG2E_F));
-    const float2 eb = make_float2(ex2_approx(el.x), ex2_approx(el.y));
-    const float2 ebi = make_float2(rcp_approx(eb.x), rcp_approx(eb.y));
-    const float2 bp = sub2(add2(eb, f2(-1.0f)), s), bm = add2(add2(ebi, f2(-1.0f)), s);
-    const float2 sp = add2(add2(f2(1.0f), sc), pp), sm = add2(sub2(f2(1.0f), sc), pm);
+    es = make_float2(ex2_approx(el.x), ex2_approx(el.y));
+    ems = make_float2(rcp_approx(es.x), rcp_approx(es.y));
+    const float2 bp = sub2(add2(es, f2(-1.0f)), s), bm = add2(add2(ems, f2(-1.0f)), s);
     const bool kx = fabsf(s.x) <= PHI_SERIES_MAX, ky = fabsf(s.y) <= PHI_SERIES_MAX;
     php = make_float2(kx ? pp.x : bp.x, ky ? pp.y : bp.y);
     phm = make_float2(kx ? pm.x : bm.x, ky ? pm.y : bm.y);
-    es = make_float2(kx ? sp.x : eb.x, ky ? sp.y : eb.y);
-    ems = make_float2(kx ? sm.x : ebi.x, ky ? sm.y : ebi.y);
 }
 
 __device__ __forceinline__ float2 tanh_small2(float2 y)
@@ -298,8 +293,8 @@ __device__ __forceinline__ void bin_f32x2(const BinsF& b, const BinsK& k, float2
     const float2 ea = mul2(vt, f2(-2.0f * LOG2E_F));
     const float2 e2 = make_float2(ex2_approx(ea.x), ex2_approx(ea.y));  // e^{-2vt}
     const float2 ope = add2(f2(1.0f), e2);
-    const float2 d = sub2(make_float2(lg2_approx(ope.x), lg2_approx(ope.y)), f2(k.lu));
-    const float2 dg = sub2(fma2(f2(k.c1), s, d), fma2(f2(k.ap), php, mul2(f2(k.am), phm)));
+    const float2 lg = make_float2(lg2_approx(ope.x), lg2_approx(ope.y));
+    const float2 dg = sub2(fma2(f2(k.c1), s, lg), fma2(f2(k.ap), php, fma2(f2(k.am), phm, f2(k.lu))));
     w = make_float2(c0 * ex2_approx(dg.x), ex2_approx(dg.y));
     if (DERIV) {
         const float2 t = add2(f2(b.tp), s);
