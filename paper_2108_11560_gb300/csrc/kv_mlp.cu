@@ -23,6 +23,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
+#include <new>
 #include <vector>
 
 #include "kv_bins.cuh"
@@ -54,6 +56,8 @@ struct kv_mlp {
     int64_t step;            // Adam steps taken
     float in_scale[4];
     float out_scale[4];
+    float* host;             // [NP] host copy of params (for the kernel-parameter weights)
+    bool host_ok;            // host matches params (false after training until refreshed)
 };
 
 namespace {
@@ -90,6 +94,8 @@ unsigned short bf16_bits_host(float f)
 int upload(kv_mlp* h, const float* host)
 {
     KV_CUDA_TRY(cudaMemcpy(h->params, host, sizeof(float) * NP, cudaMemcpyHostToDevice));
+    memcpy(h->host, host, sizeof(float) * NP);
+    h->host_ok = true;
     std::vector<unsigned short> w2(H * H);
     for (int k = 0; k < H * H; ++k) w2[k] = bf16_bits_host(host[OFF_W2 + k]);
     KV_CUDA_TRY(cudaMemcpy(h->w2h, w2.data(), sizeof(unsigned short) * H * H, cudaMemcpyHostToDevice));
@@ -108,13 +114,15 @@ int alloc_handle(kv_mlp** out)
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->w2h, sizeof(unsigned short) * H * H);
     if (e == cudaSuccess) e = cudaMemset(h->adam_m, 0, sizeof(float) * NP);
     if (e == cudaSuccess) e = cudaMemset(h->adam_s, 0, sizeof(float) * NP);
-    if (e != cudaSuccess) {
+    h->host = new (std::nothrow) float[NP];
+    if (e != cudaSuccess || !h->host) {
         cudaFree(h->params);
         cudaFree(h->adam_m);
         cudaFree(h->adam_s);
         cudaFree(h->w2h);
+        delete[] h->host;
         delete h;
-        return kvh::cuda_fail(e);
+        return e != cudaSuccess ? kvh::cuda_fail(e) : KV_ERR_NOMEM;
     }
     // feature and output scaling: a = asinh(2 v) / asinh(400) * 2 spreads small orders (v < 1)
     // over a useful share of [0, 2] for v in [0, 200]; log10 x in [-4, 4] maps to [-1, 1]
@@ -299,6 +307,15 @@ __device__ __forceinline__ PeakConst peak_constants(float v, float x, float tp, 
     return c;
 }
 
+// The small per-unit weights of layers 1 and 3, passed by value with the launch so that the
+// kernel reads them from the constant bank (operands of its FMAs) instead of shared memory.
+struct MlpConst {
+    float2 w1a[H / 2], w1b[H / 2], b1[H / 2];  // by unit pairs: {W1[u][0], W1[u+1][0]}, ...
+    float2 w3[H];                              // {W3[0][j], W3[1][j]}
+    float b3[2];
+    float in_scale[4], out_scale[4];
+};
+
 struct MlpPathParams {
     const float* v;
     const float* x;
@@ -309,10 +326,12 @@ struct MlpPathParams {
     uint8_t* status;
     int64_t n;
     int bins;
+    float inv_bins;  // 1 / bins
     float log_eps;
     uint32_t* fb_list;
     uint32_t* fb_count;
     kvh::MlpView mlp;
+    MlpConst wc;
     ExpTable exp_tab;
 };
 
@@ -425,10 +444,6 @@ struct TcSmem {
     unsigned char b[H * H * 2];      // W2 (BF16): row = output unit, K = input unit
     unsigned char bb[H * 16 * 2];    // B of layer 2's extra K slice: k = 0, 1 hold b2 split hi + lo
     unsigned char ones[8 * 16 * 2];  // A of that slice, one 8-row group read by every group: 1, 1, 0...
-    float2 w1a[H / 2], w1b[H / 2], b1[H / 2];  // layer 1 by unit pairs: {W1[u][0], W1[u+1][0]}, ...
-    float2 w3[H];                              // {W3[0][j], W3[1][j]}
-    float b3[2];
-    float in_scale[4], out_scale[4];
     float4 exp_tab[1 << kGridBits];
     uint64_t mbar;
     uint32_t tmem;
@@ -500,17 +515,6 @@ __global__ void __launch_bounds__(kMlpBlock, 7) kv_mlp_tc_kernel(MlpPathParams p
     __shared__ __align__(1024) TcSmem sm;
     const int t = threadIdx.x;
     const int warp = t >> 5;
-    for (int k = t; k < H / 2; k += kMlpBlock) {
-        sm.w1a[k] = make_float2(p.mlp.w1[4 * k], p.mlp.w1[4 * k + 2]);
-        sm.w1b[k] = make_float2(p.mlp.w1[4 * k + 1], p.mlp.w1[4 * k + 3]);
-        sm.b1[k] = make_float2(p.mlp.b1[2 * k], p.mlp.b1[2 * k + 1]);
-    }
-    for (int k = t; k < H; k += kMlpBlock) sm.w3[k] = make_float2(p.mlp.w3[k], p.mlp.w3[H + k]);
-    if (t < 2) sm.b3[t] = p.mlp.b3[t];
-    if (t < 4) {
-        sm.in_scale[t] = p.mlp.in_scale[t];
-        sm.out_scale[t] = p.mlp.out_scale[t];
-    }
     for (int k = t; k < H * H; k += kMlpBlock)
         *reinterpret_cast<unsigned short*>(sm.b + tile_off(k / H, k % H)) = p.mlp.w2h[k];
     for (int k = t; k < H * 16; k += kMlpBlock) {  // b2 = hi + lo in BF16 at k = 0, 1
@@ -554,15 +558,15 @@ __global__ void __launch_bounds__(kMlpBlock, 7) kv_mlp_tc_kernel(MlpPathParams p
         const float xa = edge ? 1.0f : x;
         // layer 1 -> BF16 row t of the A tile
         {
-            const float a = fast_asinh(va * sm.in_scale[0]) * sm.in_scale[1];
-            const float b = fmaf(__logf(xa), sm.in_scale[2], sm.in_scale[3]);
+            const float a = fast_asinh(va * p.wc.in_scale[0]) * p.wc.in_scale[1];
+            const float b = fmaf(__logf(xa), p.wc.in_scale[2], p.wc.in_scale[3]);
 #pragma unroll
             for (int c = 0; c < H / 8; ++c) {
                 uint32_t packed[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int u = 4 * c + q;  // units 2u, 2u + 1
-                    const float2 z = fma2(sm.w1a[u], f2(a), fma2(sm.w1b[u], f2(b), sm.b1[u]));
+                    const float2 z = fma2(p.wc.w1a[u], f2(a), fma2(p.wc.w1b[u], f2(b), p.wc.b1[u]));
                     // relu and round to BF16 in one conversion (unit 2u in the low half)
                     asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(packed[q]) : "f"(z.y), "f"(z.x));
                 }
@@ -585,14 +589,14 @@ __global__ void __launch_bounds__(kMlpBlock, 7) kv_mlp_tc_kernel(MlpPathParams p
         phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;");
         // layer 3 from this thread's row of the layer 2 accumulators (TMEM lane t)
-        float2 y = make_float2(sm.b3[0], sm.b3[1]);
+        float2 y = make_float2(p.wc.b3[0], p.wc.b3[1]);
 #pragma unroll
         for (int c = 0; c < H; c += 16) {
             uint32_t r[16];
             tmem_ld16(lane_base + (uint32_t)c, r);
             asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-            for (int j = 0; j < 16; ++j) y = fma2(sm.w3[c + j], f2(fmaxf(__uint_as_float(r[j]), 0.0f)), y);
+            for (int j = 0; j < 16; ++j) y = fma2(p.wc.w3[c + j], f2(fmaxf(__uint_as_float(r[j]), 0.0f)), y);
         }
         const float y0 = y.x, y1 = y.y;
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -600,8 +604,8 @@ __global__ void __launch_bounds__(kMlpBlock, 7) kv_mlp_tc_kernel(MlpPathParams p
         // their placeholder inputs), so the warp is converged when it enters the bins:
         // otherwise lanes that took a different path through the check would run the bins
         // separately, once per group.
-        const float L0 = fmaf(y0, sm.out_scale[0], sm.out_scale[1]);
-        const float L1 = fmaf(y1, sm.out_scale[2], sm.out_scale[3]);
+        const float L0 = fmaf(y0, p.wc.out_scale[0], p.wc.out_scale[1]);
+        const float L1 = fmaf(y1, p.wc.out_scale[2], p.wc.out_scale[3]);
         const float tp = peak_f32(va, xa);
         PeakConst c = peak_constants(va, xa, tp, sm.exp_tab);
         const float tr = c.b.tp;  // the grid point next to tp: the bins' reference
@@ -621,14 +625,15 @@ __global__ void __launch_bounds__(kMlpBlock, 7) kv_mlp_tc_kernel(MlpPathParams p
         }
         __syncwarp();
         c.b.s0 = t0 - c.b.tp;
-        c.b.h = (t1 - t0) / (float)p.bins;
+        c.b.h = (t1 - t0) * p.inv_bins;
         c.b.n = p.bins;
         float S0, S1, S2;
         sums_f32<1, DERIV, true>(c.b, 0, S0, S1, S2);
         if (regular && ok) {
-            df L = df_add(c.G, df_make(logf(c.b.h * S0)));
+            // log(h S0) from the approximate log2 (absolute error about 1e-7)
+            df L = df_add(c.G, df_make(lg2_approx(c.b.h * S0) * LN2_F));
             lk = L.hi + L.lo;
-            const float r = 1.0f / S0;
+            const float r = rcp_approx(S0);
             dv = DERIV ? copysignf(S1 * r, v) : 0.0f;
             if (v == 0.0f) dv = 0.0f;
             dx = DERIV ? -(S2 * r) : 0.0f;
@@ -980,6 +985,34 @@ int mlp_view(const kv_mlp* h, MlpView* out)
     return KV_OK;
 }
 
+// The kernel-parameter weights from the handle's host copy, refreshed from the device (ordered on
+// `s`) after training moved the parameters on.
+int fill_mlp_const(const kv_mlp* hc, cudaStream_t s, MlpConst* c)
+{
+    static std::mutex refresh;
+    kv_mlp* h = const_cast<kv_mlp*>(hc);
+    {
+        std::lock_guard<std::mutex> lock(refresh);
+        if (!h->host_ok) {
+            KV_CUDA_TRY(cudaMemcpyAsync(h->host, h->params, sizeof(float) * NP, cudaMemcpyDeviceToHost, s));
+            KV_CUDA_TRY(cudaStreamSynchronize(s));
+            h->host_ok = true;
+        }
+    }
+    const float* w = h->host;
+    for (int k = 0; k < H / 2; ++k) {
+        c->w1a[k] = make_float2(w[OFF_W1 + 4 * k], w[OFF_W1 + 4 * k + 2]);
+        c->w1b[k] = make_float2(w[OFF_W1 + 4 * k + 1], w[OFF_W1 + 4 * k + 3]);
+        c->b1[k] = make_float2(w[OFF_B1 + 2 * k], w[OFF_B1 + 2 * k + 1]);
+    }
+    for (int k = 0; k < H; ++k) c->w3[k] = make_float2(w[OFF_W3 + k], w[OFF_W3 + H + k]);
+    c->b3[0] = w[OFF_B3];
+    c->b3[1] = w[OFF_B3 + 1];
+    memcpy(c->in_scale, h->in_scale, sizeof(c->in_scale));
+    memcpy(c->out_scale, h->out_scale, sizeof(c->out_scale));
+    return KV_OK;
+}
+
 int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, uint32_t* scratch_in)
 {
     if (a->n > (int64_t)0xffffffffll) return KV_ERR_SIZE;
@@ -994,7 +1027,10 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
     p.go = (const float*)a->grad_out;
     p.status = a->status;
     p.n = a->n;
+    rc = fill_mlp_const(a->mlp, (cudaStream_t)a->stream, &p.wc);
+    if (rc != KV_OK) return rc;
     p.bins = bins;
+    p.inv_bins = 1.0f / (float)bins;
     p.log_eps = (float)log_eps;
     p.exp_tab = exp_table();
     cudaStream_t s = (cudaStream_t)a->stream;
@@ -1069,6 +1105,7 @@ int kv_mlp_free(kv_mlp* h)
     cudaFree(h->adam_m);
     cudaFree(h->adam_s);
     cudaFree(h->w2h);
+    delete[] h->host;
     h->magic = 0;
     delete h;
     return KV_OK;
@@ -1205,6 +1242,7 @@ int kv_mlp_train(kv_mlp* h, const kv_train_args* a)
     float* partial = nullptr;
     KV_CUDA_TRY(cudaMallocAsync((void**)&partial, sizeof(float) * (size_t)nb * (NP + 1), s));
     int rc = KV_OK;
+    if (a->steps > 0) h->host_ok = false;  // the device copy moves on; refreshed at the next use
     for (int j = 0; j < a->steps && rc == KV_OK; ++j) {
         const int64_t t = h->step + 1;
         rc = run_grad(h, a->v, a->x, a->t0, a->t1, a->n, a->batch, h->step, a->seed, 0, partial, s);

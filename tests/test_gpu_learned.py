@@ -86,6 +86,26 @@ def test_adam_steps_match_oracle():
     assert d.max() < 10 * lr
 
 
+def test_fast_path_sees_trained_weights(net):
+    """The fast path reads the small layers' weights from a host copy of the parameters: after
+    training steps on the device, its results equal those of a fresh handle given the trained
+    parameters (and differ from the untrained ones)."""
+    v, x = W.hard_band(50000, seed=312)
+    vf, xf = _t(v, torch.float32), _t(x, torch.float32)
+    m = learned.Mlp.create(0)
+    m.set_params(net.params())
+    before = kv.kv_fwd_bwd_ex(vf, xf, bins=32, bracket="mlp", mlp=m, status=True)
+    tv, tx, t0, t1 = learned.training_set(DEV, n=8192, seed=313)
+    m.train(tv, tx, t0, t1, steps=20, batch=1024, lr=1e-2, seed=3)
+    after = kv.kv_fwd_bwd_ex(vf, xf, bins=32, bracket="mlp", mlp=m, status=True)
+    fresh = learned.Mlp.create(0)
+    fresh.set_params(m.params())
+    ref = kv.kv_fwd_bwd_ex(vf, xf, bins=32, bracket="mlp", mlp=fresh, status=True)
+    for k in ("logk", "dv", "dx", "status"):
+        assert torch.equal(after[k], ref[k]), k
+    assert not torch.equal(after["status"], before["status"]) or not torch.equal(after["logk"], before["logk"])
+
+
 def test_checkpoint_roundtrip(net):
     with tempfile.TemporaryDirectory() as d:
         path = os.path.join(d, "net.kvmlp")
