@@ -250,6 +250,9 @@ struct ExpTable {
     float4 e[1 << kGridBits];  // {hi, lo} of 2^{i/128}, then {hi, lo} of 2^{-i/128}
 };
 
+// The table on each device (read through the L1 cache), filled once per device.
+__device__ float4 g_exp_tab[1 << kGridBits];
+
 const ExpTable& exp_table()
 {
     static const ExpTable t = [] {
@@ -262,6 +265,21 @@ const ExpTable& exp_table()
         return r;
     }();
     return t;
+}
+
+int ensure_exp_table()
+{
+    static std::mutex mu;
+    static bool ready[64];
+    int dev = 0;
+    KV_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return KV_ERR_ARG;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ready[dev]) {
+        KV_CUDA_TRY(cudaMemcpyToSymbol(g_exp_tab, exp_table().e, sizeof(ExpTable)));
+        ready[dev] = true;
+    }
+    return KV_OK;
 }
 
 // 2^k for |k| <= 126 (exact); larger |k| saturates (inf or the smallest normal).
@@ -282,7 +300,7 @@ __device__ __forceinline__ PeakConst peak_constants(float v, float x, float tp, 
     PeakConst c;
     const float j = rintf(tp * kGridInv);
     const int ji = (int)j;
-    const float4 T = tab[ji & ((1 << kGridBits) - 1)];
+    const float4 T = __ldg(&tab[ji & ((1 << kGridBits) - 1)]);
     const float p2 = pow2i(ji >> kGridBits), p2i = pow2i(-(ji >> kGridBits));
     const df E{T.x * p2, T.y * p2}, Ei{T.z * p2i, T.w * p2i};  // e^{t_r}, e^{-t_r}
     df tr = two_prod(j, kGridStepHi);
@@ -332,7 +350,6 @@ struct MlpPathParams {
     uint32_t* fb_count;
     kvh::MlpView mlp;
     MlpConst wc;
-    ExpTable exp_tab;
 };
 
 constexpr int kMlpBlock = 128;
@@ -444,7 +461,6 @@ struct TcSmem {
     unsigned char b[H * H * 2];      // W2 (BF16): row = output unit, K = input unit
     unsigned char bb[H * 16 * 2];    // B of layer 2's extra K slice: k = 0, 1 hold b2 split hi + lo
     unsigned char ones[8 * 16 * 2];  // A of that slice, one 8-row group read by every group: 1, 1, 0...
-    float4 exp_tab[1 << kGridBits];
     uint64_t mbar;
     uint32_t tmem;
 };
@@ -510,7 +526,7 @@ constexpr uint32_t kTmemCols = 64;
 // than the 128 FMAs it saves.)  A wait that does not finish within its limit sends the CTA's
 // remaining pairs to the fallback list (correct, slower) instead of hanging.
 template <bool DERIV>
-__global__ void __launch_bounds__(kMlpBlock, 7) kv_mlp_tc_kernel(MlpPathParams p)
+__global__ void __launch_bounds__(kMlpBlock, 8) kv_mlp_tc_kernel(MlpPathParams p)
 {
     __shared__ __align__(1024) TcSmem sm;
     const int t = threadIdx.x;
@@ -526,7 +542,6 @@ __global__ void __launch_bounds__(kMlpBlock, 7) kv_mlp_tc_kernel(MlpPathParams p
     }
     if (t < 8 * 16)
         *reinterpret_cast<unsigned short*>(sm.ones + slice_off(t >> 4, t & 15)) = (t & 15) < 2 ? 0x3F80 : 0;
-    for (int k = t; k < (1 << kGridBits); k += kMlpBlock) sm.exp_tab[k] = p.exp_tab.e[k];
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.mbar)));
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -607,7 +622,7 @@ __global__ void __launch_bounds__(kMlpBlock, 7) kv_mlp_tc_kernel(MlpPathParams p
         const float L0 = fmaf(y0, p.wc.out_scale[0], p.wc.out_scale[1]);
         const float L1 = fmaf(y1, p.wc.out_scale[2], p.wc.out_scale[3]);
         const float tp = peak_f32(va, xa);
-        PeakConst c = peak_constants(va, xa, tp, sm.exp_tab);
+        PeakConst c = peak_constants(va, xa, tp, g_exp_tab);
         const float tr = c.b.tp;  // the grid point next to tp: the bins' reference
         // the predicted range [tp - w0, tp + w1] as distances below and above tr
         const float w0 = fmaxf(fmaxf(__expf(L0) - DELTA, 0.0f) - (tp - tr), 0.0f);
@@ -1032,7 +1047,8 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
     p.bins = bins;
     p.inv_bins = 1.0f / (float)bins;
     p.log_eps = (float)log_eps;
-    p.exp_tab = exp_table();
+    rc = ensure_exp_table();
+    if (rc != KV_OK) return rc;
     cudaStream_t s = (cudaStream_t)a->stream;
     // scratch: the fallback list and its counter (the caller's, or allocated on the stream)
     uint32_t* scratch = scratch_in;
