@@ -40,20 +40,22 @@ WORKLOAD = "hard_band_16M"
 MIXED_LOG_EPS = -20.0
 
 # Algorithmic FP32 work of the learned-bracket fast path, counted operation by operation from
-# its formulas with an FMA as one operation (derivation in the design notes):
-#   per bin: phi(+-s) 29, the difference g - g(t_p) and its weight 10, three block-compensated
-#            sums 5.25, the two derivative integrands 9, the bin's abscissa 1   -> 55 (+ 6 MUFU)
-#   per pair: features and layer 1 ~150, layer 3 192, peak Newton ~115, float-float offset and
-#             constants ~430, endpoint check ~55, setup and epilogue ~30         -> 971
-# (the 64x64 hidden layer runs on the tensor cores and is not counted here).  ncu's executed
-# FFMA + FADD + FMUL counters agree: 55.2 per bin and 971 per pair (4M pairs at 1 and 32 bins).
-FP32_OPS_PER_BIN = 55
+# its formulas with an FMA as one operation and a paired (f32x2) instruction as two:
+#   per bin: the abscissa 1, phi(+-s) and e^{+-s} 20, the exponent g - g(t_p) and its inputs 7,
+#            the two derivative integrands 8 (+ the tanh series in the ~37 % of warp-blocks that
+#            need it, ~2.6), three block-compensated sums 5.25              -> 44 (+ 6 MUFU)
+#   per pair: layer 1 and layer 3 on the CUDA cores 256 (layer 2 runs on the tensor cores and
+#             is not counted), peak Newton, offset constants, endpoint check, setup and finish
+#             ~260                                                            -> 514
+# ncu's executed FFMA + FADD + FMUL (+ 2 x FFMA2/FADD2/FMUL2) counters over 4M pairs at 1 and 32
+# bins give 44.16 per bin and 513.5 per pair (profiles/kv_mlp_tc_kernel_hard_band_4M.md).
+FP32_OPS_PER_BIN = 44.16
 MUFU_OPS_PER_BIN = 6
-FP32_OPS_PER_PAIR = 971
-# DRAM bytes per pair of the fast-path kernel, from one ncu capture (50.41 MB read + 8.96 MB
+FP32_OPS_PER_PAIR = 513.5
+# DRAM bytes per pair of the fast-path kernel, from one ncu capture (50.39 MB read + 8.68 MB
 # written for 4,194,304 pairs; profiles/kv_mlp_tc_kernel_hard_band_4M.md), scaled to a launch.
 # Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES_PER_PAIR = (50.411520e6 + 8.958464e6) / 4194304
+TRAFFIC_BYTES_PER_PAIR = (50.387456e6 + 8.675584e6) / 4194304
 
 
 def _peaks():
