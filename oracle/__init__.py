@@ -114,7 +114,7 @@ def _lib(precision: str) -> ctypes.CDLL:
             P = ctypes.c_void_p
             f = getattr(lib, f"kv_oracle_o1_{sfx}")
             f.argtypes = [P, P, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                          ctypes.c_double, ctypes.c_int, P, P, P, P, ctypes.c_int]
+                          ctypes.c_double, ctypes.c_int, P, P, P, P, P, ctypes.c_int]
             f.restype = None
             f = getattr(lib, f"kv_oracle_g_{sfx}")
             f.argtypes = [ctypes.c_double, ctypes.c_double, P, ctypes.c_int64, P, P, P]
@@ -125,7 +125,7 @@ def _lib(precision: str) -> ctypes.CDLL:
                           ctypes.c_int, ctypes.c_int, P]
             f.restype = None
             if precision == "long":
-                lib.kv_oracle_dense.argtypes = [P, P, ctypes.c_int64, P, P, P, ctypes.c_int]
+                lib.kv_oracle_dense.argtypes = [P, P, ctypes.c_int64, P, P, P, P, ctypes.c_int]
                 lib.kv_oracle_dense.restype = None
             _LIBS[precision] = lib
         return _LIBS[precision]
@@ -141,11 +141,13 @@ def _as_f64(a) -> np.ndarray:
 
 def o1(v, x, bins: int = 128, log_eps: float = LOG_EPS_F64, max_iter: int = MAX_ITER,
        tol: float = 0.0, max_range: int = MAX_RANGE, precision: str = "double",
-       threads: int = 0, bracket: bool = False) -> dict:
+       threads: int = 0, bracket: bool = False, second: bool = False) -> dict:
     """The fixed-bin method (Algorithm 3) on arrays of (v, x).
 
-    Returns a dict of float64 arrays ``logk``, ``dv``, ``dx`` and, with ``bracket=True``,
-    ``t0``, ``tp``, ``t1``, ``G`` (= g(t_p)).  ``threads=0`` uses every host core.
+    Returns a dict of float64 arrays ``logk``, ``dv``, ``dx``; with ``bracket=True`` also
+    ``t0``, ``tp``, ``t1``, ``G`` (= g(t_p)); with ``second=True`` also the second derivatives
+    of log K, ``d2v`` (d2/dv2), ``dvx`` (d2/dv dx) and ``d2x`` (d2/dx2), from the same bins
+    (Sec. 4.1).  ``threads=0`` uses every host core.
     """
     v = _as_f64(v)
     x = _as_f64(x)
@@ -158,28 +160,39 @@ def o1(v, x, bins: int = 128, log_eps: float = LOG_EPS_F64, max_iter: int = MAX_
     dv = np.empty(n)
     dx = np.empty(n)
     brk = np.empty(4 * n) if bracket else None
+    d2 = np.empty(3 * n) if second else None
     lib = _lib(precision)
     sfx = "d" if precision == "double" else "ld"
     getattr(lib, f"kv_oracle_o1_{sfx}")(
         _ptr(v), _ptr(x), n, bins, log_eps, max_iter, tol, max_range, _ptr(logk), _ptr(dv),
-        _ptr(dx), _ptr(brk) if bracket else None, threads)
+        _ptr(dx), _ptr(brk) if bracket else None, _ptr(d2) if second else None, threads)
     out = {"logk": logk, "dv": dv, "dx": dx}
     if bracket:
         b = brk.reshape(n, 4)
         out.update(t0=b[:, 0].copy(), tp=b[:, 1].copy(), t1=b[:, 2].copy(), G=b[:, 3].copy())
+    if second:
+        d = d2.reshape(n, 3)
+        out.update(d2v=d[:, 0].copy(), dvx=d[:, 1].copy(), d2x=d[:, 2].copy())
     return out
 
 
-def dense(v, x, threads: int = 0) -> dict:
-    """log K, d/dv log K, d/dx log K by adaptive Gauss-Legendre quadrature in long double."""
+def dense(v, x, threads: int = 0, second: bool = False) -> dict:
+    """log K, d/dv log K, d/dx log K (and with ``second=True`` d2v, dvx, d2x) by adaptive
+    Gauss-Legendre quadrature in long double."""
     v = _as_f64(v)
     x = _as_f64(x)
     n = v.size
     logk = np.empty(n)
     dv = np.empty(n)
     dx = np.empty(n)
-    _lib("long").kv_oracle_dense(_ptr(v), _ptr(x), n, _ptr(logk), _ptr(dv), _ptr(dx), threads)
-    return {"logk": logk, "dv": dv, "dx": dx}
+    d2 = np.empty(3 * n) if second else None
+    _lib("long").kv_oracle_dense(_ptr(v), _ptr(x), n, _ptr(logk), _ptr(dv), _ptr(dx),
+                                 _ptr(d2) if second else None, threads)
+    out = {"logk": logk, "dv": dv, "dx": dx}
+    if second:
+        d = d2.reshape(n, 3)
+        out.update(d2v=d[:, 0].copy(), dvx=d[:, 1].copy(), d2x=d[:, 2].copy())
+    return out
 
 
 def g_eval(v: float, x: float, t, precision: str = "double"):

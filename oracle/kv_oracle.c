@@ -14,6 +14,10 @@
  *       Algorithm 3 (LogBesselK).  The derivatives follow Sec. 4.1: the same bins carry the
  *       v-derivative integrand t sinh(vt) e^{-x cosh t} and the x-derivative integrand
  *       -cosh(t) cosh(vt) e^{-x cosh t}, each divided by the K sum.
+ *       Second derivatives (Sec. 4.1, the integrands f^{(n,m)} with n + m = 2) come from the
+ *       same bins: K_vv, K_vx, K_xx carry t^2 cosh(vt), -t cosh(t) sinh(vt) and cosh^2(t) cosh(vt)
+ *       times e^{-x cosh t}, and the log-derivatives are their plain combinations
+ *       d2/dv2 log K = K_vv/K - (K_v/K)^2 and likewise (reading R8).
  *       The file is compiled twice: with KV_REAL = double (the method in FP64, as the paper
  *       runs it) and with KV_REAL = long double (the same steps in wider arithmetic, used as the
  *       method's reference value at FP64 tolerances).  <tgmath.h> picks exp/expl etc. by type.
@@ -40,6 +44,8 @@
  *      log K = +inf, d/dv = 0 if v = 0 else +-inf, d/dx = -inf; x = +inf gives log K = -inf,
  *      d/dv = +-0, d/dx = -1; |v| = inf with finite x > 0 gives +inf, +-inf, -inf;
  *      x < 0 or a NaN gives NaN in all three outputs.
+ *   R8 Second derivatives reuse the forward range too; x = +inf gives 0 for all three, every
+ *      other edge input gives NaN.  d2/dv dx log K is odd in v (0 at v = 0), the other two even.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -175,11 +181,19 @@ static int edge_case(double v, double x, double* logk, double* dv, double* dx)
 
 /* ---------------------------------------------------------------- Algorithm 3 + Eq. (int) */
 /* One pair through the method.  brk (may be NULL) receives t0, t_p, t1, g(t_p). */
+/* Second derivatives of an edge input (reading R8). */
+static void edge_case2(double x, double* d2)
+{
+    const double z = isinf(x) && x > 0 ? 0.0 : NAN;
+    d2[0] = d2[1] = d2[2] = z;
+}
+
 static void o1_pair(double v_in, double x_in, int bins, double log_eps, int max_iter, double tol,
-                    int max_range, double* logk, double* dv, double* dx, double* brk)
+                    int max_range, double* logk, double* dv, double* dx, double* brk, double* d2)
 {
     if (edge_case(v_in, x_in, logk, dv, dx)) {
         if (brk) brk[0] = brk[1] = brk[2] = brk[3] = NAN;
+        if (d2) edge_case2(x_in, d2);
         return;
     }
     pair_t p;
@@ -210,7 +224,7 @@ static void o1_pair(double v_in, double x_in, int bins, double log_eps, int max_
 
     /* Sec. 2.4 Eq. (int), reading R5; Sec. 4.1 derivative integrands, reading R6. */
     real h = (t1 - t0) / bins;
-    real s0 = 0, s1 = 0, s2 = 0;
+    real s0 = 0, s1 = 0, s2 = 0, svv = 0, svx = 0, sxx = 0;
     for (int m = 0; m <= bins; m++) {
         real t = t0 + m * h;
         real c = (m == 0 || m == bins) ? (real)0.5 : (real)1;
@@ -218,10 +232,22 @@ static void o1_pair(double v_in, double x_in, int bins, double log_eps, int max_
         s0 += w;
         s1 += w * t * tanh(p.v * t);
         s2 += w * cosh(t);
+        if (d2) {
+            svv += w * t * t;                          /* K_vv / (cosh(vt) e^{-x cosh t}) */
+            svx += w * t * tanh(p.v * t) * cosh(t);    /* -K_vx / ... */
+            sxx += w * cosh(t) * cosh(t);              /* K_xx / ... */
+        }
     }
     *logk = (double)(p.G + log(h) + log(s0));
     *dv = (double)(sign * (s1 / s0));
     *dx = (double)(-(s2 / s0));
+    if (d2) {
+        /* reading R8: plain combinations of the same sums */
+        const real ev = s1 / s0, ex = s2 / s0;
+        d2[0] = (double)(svv / s0 - ev * ev);
+        d2[1] = (double)(sign * (ex * ev - svx / s0));
+        d2[2] = (double)(sxx / s0 - ex * ex);
+    }
     if (brk) {
         brk[0] = (double)t0;
         brk[1] = (double)tp;
@@ -239,16 +265,17 @@ static void set_threads(int nthreads)
 #endif
 }
 
-/* Batched O1.  brk: NULL or 4 doubles per pair (t0, t_p, t1, g(t_p)). */
+/* Batched O1.  brk: NULL or 4 doubles per pair (t0, t_p, t1, g(t_p)); d2: NULL or 3 doubles per
+ * pair (d2/dv2, d2/dv dx, d2/dx2 of log K). */
 void KV_NAME(kv_oracle_o1)(const double* v, const double* x, int64_t n, int bins, double log_eps,
                            int max_iter, double tol, int max_range, double* logk, double* dv,
-                           double* dx, double* brk, int nthreads)
+                           double* dx, double* brk, double* d2, int nthreads)
 {
     set_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t i = 0; i < n; i++)
         o1_pair(v[i], x[i], bins, log_eps, max_iter, tol, max_range, logk + i, dv + i, dx + i,
-                brk ? brk + 4 * i : NULL);
+                brk ? brk + 4 * i : NULL, d2 ? d2 + 3 * i : NULL);
 }
 
 /* Plain evaluation of g, g', g'' (for bracket invariant checks in the tests). */
@@ -328,47 +355,57 @@ static long double dense_g(const dense_t* d, long double t)
     return a + log1pl(expl(-2 * a)) - logl(2.0L) - d->x * coshl(t);
 }
 
-/* integrals over [a, b] of e^{g - gmax} * {1, t tanh(vt), cosh t} by one GL panel */
-static void gl_panel(const dense_t* d, long double a, long double b, long double out[3])
+/* integrals over [a, b] of e^{g - gmax} * {1, t tanh(vt), cosh t, t^2, t tanh(vt) cosh t,
+ * cosh^2 t} by one GL panel */
+#define NQ 6
+static void gl_panel(const dense_t* d, long double a, long double b, long double out[NQ])
 {
     long double c = (a + b) / 2, r = (b - a) / 2;
-    out[0] = out[1] = out[2] = 0;
+    for (int k = 0; k < NQ; k++) out[k] = 0;
     for (int i = 0; i < GL_N; i++) {
         long double t = c + r * gl_z[i];
         long double e = expl(dense_g(d, t) - d->gmax) * gl_w[i];
+        long double th = tanhl(d->v * t), ch = coshl(t);
         out[0] += e;
-        out[1] += e * t * tanhl(d->v * t);
-        out[2] += e * coshl(t);
+        out[1] += e * t * th;
+        out[2] += e * ch;
+        out[3] += e * t * t;
+        out[4] += e * t * th * ch;
+        out[5] += e * ch * ch;
     }
-    for (int k = 0; k < 3; k++) out[k] *= r;
+    for (int k = 0; k < NQ; k++) out[k] *= r;
 }
 
 /* Adaptive bisection of [a, b]: a panel is accepted when its 20-point estimate and the sum of its
  * two halves agree to the panel's share of the tolerance, or to the rounding noise of the
  * integrand (about noise * |value|); at most 2^30 subdivisions deep. */
-static void gl_adapt(const dense_t* d, long double a, long double b, const long double whole[3],
-                     const long double tol[3], long double noise, int depth, long double acc[3])
+static void gl_adapt(const dense_t* d, long double a, long double b, const long double whole[NQ],
+                     const long double tol[NQ], long double noise, int depth, long double acc[NQ])
 {
-    long double m = (a + b) / 2, l[3], r[3];
+    long double m = (a + b) / 2, l[NQ], r[NQ];
     gl_panel(d, a, m, l);
     gl_panel(d, m, b, r);
     int ok = 1;
-    for (int k = 0; k < 3; k++) {
+    for (int k = 0; k < NQ; k++) {
         long double floor_k = noise * fabsl(l[k] + r[k]);
         if (fabsl(l[k] + r[k] - whole[k]) > fmaxl(tol[k], floor_k)) ok = 0;
     }
     if (ok || depth >= 30) {
-        for (int k = 0; k < 3; k++) acc[k] += l[k] + r[k];
+        for (int k = 0; k < NQ; k++) acc[k] += l[k] + r[k];
         return;
     }
-    long double half_tol[3] = {tol[0] / 2, tol[1] / 2, tol[2] / 2};
+    long double half_tol[NQ];
+    for (int k = 0; k < NQ; k++) half_tol[k] = tol[k] / 2;
     gl_adapt(d, a, m, l, half_tol, noise, depth + 1, acc);
     gl_adapt(d, m, b, r, half_tol, noise, depth + 1, acc);
 }
 
-static void o2_pair(double v_in, double x_in, double* logk, double* dv, double* dx)
+static void o2_pair(double v_in, double x_in, double* logk, double* dv, double* dx, double* d2)
 {
-    if (edge_case(v_in, x_in, logk, dv, dx)) return;
+    if (edge_case(v_in, x_in, logk, dv, dx)) {
+        if (d2) edge_case2(x_in, d2);
+        return;
+    }
     dense_t d;
     d.v = fabsl((long double)v_in);
     d.x = (long double)x_in;
@@ -394,28 +431,35 @@ static void o2_pair(double v_in, double x_in, double* logk, double* dv, double* 
         a = tstar - step > 0 ? tstar - step : 0;
     }
     /* coarse total for the tolerance scale: 64 panels */
-    long double total[3] = {0, 0, 0}, pan[3];
+    long double total[NQ] = {0}, pan[NQ];
     for (int i = 0; i < 64; i++) {
         gl_panel(&d, a + (b - a) * i / 64, a + (b - a) * (i + 1) / 64, pan);
-        for (int k = 0; k < 3; k++) total[k] += pan[k];
+        for (int k = 0; k < NQ; k++) total[k] += pan[k];
     }
-    long double tol[3], whole[3], acc[3] = {0, 0, 0};
-    for (int k = 0; k < 3; k++) tol[k] = 1e-18L * fabsl(total[k]);
+    long double tol[NQ], whole[NQ], acc[NQ] = {0};
+    for (int k = 0; k < NQ; k++) tol[k] = 1e-18L * fabsl(total[k]);
     /* g is evaluated as the difference of terms up to |g(t_max)| + x cosh(b) in size */
     long double noise = 64 * LDBL_EPSILON * (1 + fabsl(gstar) + d.x * coshl(b) + d.v * b);
     gl_panel(&d, a, b, whole);
     gl_adapt(&d, a, b, whole, tol, noise, 0, acc);
+    const long double sign = v_in < 0 ? -1 : 1;
     *logk = (double)(gstar + logl(acc[0]));
-    *dv = (double)((v_in < 0 ? -1 : 1) * (acc[1] / acc[0]));
+    *dv = (double)(sign * (acc[1] / acc[0]));
     *dx = (double)(-(acc[2] / acc[0]));
+    if (d2) {
+        const long double ev = acc[1] / acc[0], ex = acc[2] / acc[0];
+        d2[0] = (double)(acc[3] / acc[0] - ev * ev);
+        d2[1] = (double)(sign * (ex * ev - acc[4] / acc[0]));
+        d2[2] = (double)(acc[5] / acc[0] - ex * ex);
+    }
 }
 
 void kv_oracle_dense(const double* v, const double* x, int64_t n, double* logk, double* dv,
-                     double* dx, int nthreads)
+                     double* dx, double* d2, int nthreads)
 {
     gl_init();
     set_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int64_t i = 0; i < n; i++) o2_pair(v[i], x[i], logk + i, dv + i, dx + i);
+    for (int64_t i = 0; i < n; i++) o2_pair(v[i], x[i], logk + i, dv + i, dx + i, d2 ? d2 + 3 * i : NULL);
 }
 #endif

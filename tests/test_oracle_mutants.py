@@ -45,9 +45,18 @@ MUTANTS = [
     ("x = inf gives d/dx = 0", "*dx = -1.0;", "*dx = 0.0;"),
     ("x = 0 loses the sign of v", "*dv = (v == 0) ? 0.0 : copysign(INFINITY, v);", "*dv = (v == 0) ? 0.0 : INFINITY;"),
     ("Gauss-Legendre weights halved", "gl_w[i] = 2 / ((1 - z * z) * dp * dp);", "gl_w[i] = 1 / ((1 - z * z) * dp * dp);"),
-    ("Gauss-Legendre panel not scaled", "for (int k = 0; k < 3; k++) out[k] *= r;", ""),
-    ("dense d/dv integrand without t", "out[1] += e * t * tanhl(d->v * t);", "out[1] += e * tanhl(d->v * t);"),
+    ("Gauss-Legendre panel not scaled", "for (int k = 0; k < NQ; k++) out[k] *= r;", ""),
+    ("dense d/dv integrand without t", "out[1] += e * t * th;", "out[1] += e * th;"),
     ("dense range starts at the peak", "a = tstar - step > 0 ? tstar - step : 0;", "a = tstar;"),
+    ("K_vv integrand with t for t^2", "svv += w * t * t;", "svv += w * t;"),
+    ("K_vx integrand without cosh t", "svx += w * t * tanh(p.v * t) * cosh(t);", "svx += w * t * tanh(p.v * t);"),
+    ("K_xx integrand with cosh t once", "sxx += w * cosh(t) * cosh(t);", "sxx += w * cosh(t);"),
+    ("d2v without the square of d/dv", "d2[0] = (double)(svv / s0 - ev * ev);", "d2[0] = (double)(svv / s0);"),
+    ("dvx not odd in v", "d2[1] = (double)(sign * (ex * ev - svx / s0));", "d2[1] = (double)((ex * ev - svx / s0));"),
+    ("dvx with the product's sign flipped", "d2[1] = (double)(sign * (ex * ev - svx / s0));", "d2[1] = (double)(sign * (-ex * ev - svx / s0));"),
+    ("dense K_xx integrand with cosh t once", "out[5] += e * ch * ch;", "out[5] += e * ch;"),
+    ("dense d2x plus the square", "d2[2] = (double)(acc[5] / acc[0] - ex * ex);", "d2[2] = (double)(acc[5] / acc[0] + ex * ex);"),
+    ("second derivatives 0 for every edge input", "const double z = isinf(x) && x > 0 ? 0.0 : NAN;", "const double z = 0.0;"),
 ]
 
 # the pins run against each mutant (the ones that take well under a second each)
@@ -67,6 +76,13 @@ PINS = [
     pins.test_findrange_and_findzero_alone,
     pins.test_findzero_keeps_the_zero_bracketed,
     pins.test_edge_cases,
+    lambda: pins.test_second_dx_half_integer_closed_form(1),
+    pins.test_second_dx_bessel_equation,
+    pins.test_second_dvx_recurrence_identity,
+    pins.test_second_dv_mpmath_quadrature,
+    pins.test_second_derivatives_symmetry_and_signs,
+    pins.test_second_derivatives_o1_against_dense,
+    pins.test_second_derivatives_edge_cases,
 ]
 
 

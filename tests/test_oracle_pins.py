@@ -397,3 +397,110 @@ def test_paper_error_metric():
     # relative deviation in units of eps (log K itself, as the paper compares values of K)
     assert np.median(err(o["logk"], d["logk"])) < 1
     assert np.median(err(o["dx"], d["dx"])) < 1
+
+
+# ------------------------------------------------------------------ second derivatives (Sec. 4.1, n + m = 2)
+
+@pytest.mark.parametrize("k", [0, 1, 3, 6])
+def test_second_dx_half_integer_closed_form(k):
+    """d2/dx2 log K_{k+1/2}(x) by mpmath differentiation of the elementary closed form
+    (for k = 0 it is 1/(2x^2))."""
+    xs = np.array([1e-3, 0.05, 0.7, 3.0, 40.0, 300.0, 1e4])
+    ref = np.array([float(mpmath.diff(lambda t: _log_k_half(k, t), mpmath.mpf(xx), 2)) for xx in xs])
+    if k == 0:
+        assert np.allclose(ref, 1 / (2 * xs ** 2), rtol=4e-16, atol=0)
+    for name, out in (("o1_long", oracle.o1(np.full_like(xs, k + 0.5), xs, precision="long", second=True)),
+                      ("dense", oracle.dense(np.full_like(xs, k + 0.5), xs, second=True))):
+        # the plain combination E[cosh^2] - E[cosh]^2 cancels to ~1/(2x^2): the sums of ~130
+        # terms in long double (2^-64) leave about 130 2^-64 E[cosh]^2 absolute in it
+        tol = 1e-12 + 1e3 * 2.0 ** -64 * out["dx"] ** 2 / ref
+        assert np.all(rel(out["d2x"], ref) < tol), (name, rel(out["d2x"], ref))
+
+
+def test_second_dx_bessel_equation():
+    """x^2 K'' + x K' - (x^2 + v^2) K = 0 in log form: L'' = 1 + v^2/x^2 - L'/x - L'^2, with L'
+    the (pinned) first derivative, on the whole target domain."""
+    v, x = W.full_domain(300, seed=120)
+    o = oracle.o1(v, x, precision="long", second=True)
+    d1 = o["dx"]
+    rhs = 1 + (v / x) ** 2 - d1 / x - d1 * d1
+    scale = 1 + (v / x) ** 2 + np.abs(d1) / x + d1 * d1
+    assert np.max(np.abs(o["d2x"] - rhs) / scale) < 1e-14
+
+
+def test_second_dvx_recurrence_identity():
+    """d/dx log K_v = -v/x - R with R = K_{v-1}/K_v (Eq. deriv, corrected); its v-derivative:
+    d2/dv dx log K_v = -1/x - R (d/dv log K_{v-1} - d/dv log K_v)."""
+    rng = np.random.default_rng(121)
+    v = rng.uniform(0.0, 300.0, 300)
+    x = 10 ** rng.uniform(-4, 4, 300)
+    a = oracle.o1(v, x, precision="long", second=True)
+    b = oracle.o1(v - 1, x, precision="long")
+    R = np.exp(b["logk"] - a["logk"])
+    rhs = -1 / x - R * (b["dv"] - a["dv"])
+    scale = 1 / x + R * (np.abs(b["dv"]) + np.abs(a["dv"]))
+    assert np.max(np.abs(a["dvx"] - rhs) / scale) < 1e-12
+
+
+def _mp_second_v(v, x):
+    """d2/dv2 log K by mpmath quadrature of K, K_v and K_vv (30 digits)."""
+    v = mpmath.mpf(v)
+    x = mpmath.mpf(x)
+    f = lambda t: mpmath.exp(-x * mpmath.cosh(t))
+    top = max(float(mpmath.asinh(v / x)), float(mpmath.acosh(1 + 80 / x))) + 2
+    pts = [mpmath.mpf(p) for p in np.linspace(0, top, 129)]  # panels narrower than the peak
+    K = mpmath.quad(lambda t: mpmath.cosh(v * t) * f(t), pts)
+    Kv = mpmath.quad(lambda t: t * mpmath.sinh(v * t) * f(t), pts)
+    Kvv = mpmath.quad(lambda t: t * t * mpmath.cosh(v * t) * f(t), pts)
+    return float(Kvv / K - (Kv / K) ** 2)
+
+
+def test_second_dv_mpmath_quadrature():
+    """d2/dv2 log K against an independent mpmath quadrature at small orders."""
+    mpmath.mp.dps = 30
+    try:
+        pts = [(0.0, 0.3), (0.5, 1.0), (2.5, 0.05), (7.0, 20.0), (15.0, 3.0), (30.0, 100.0)]
+        ref = np.array([_mp_second_v(a, b) for a, b in pts])
+    finally:
+        mpmath.mp.dps = 40
+    v = np.array([p[0] for p in pts])
+    x = np.array([p[1] for p in pts])
+    for out in (oracle.o1(v, x, precision="long", second=True), oracle.dense(v, x, second=True)):
+        assert rel(out["d2v"], ref).max() < 1e-12
+
+
+def test_second_derivatives_symmetry_and_signs():
+    """d2v and d2x are even in v, dvx is odd and 0 at v = 0; d2x > 0 (log K is convex in x)
+    and d2v > 0 (K_v(x) is log-convex in v)."""
+    v, x = W.full_domain(300, seed=122)
+    a = oracle.o1(v, x, precision="long", second=True)
+    b = oracle.o1(-v, x, precision="long", second=True)
+    assert np.array_equal(a["d2v"], b["d2v"]) and np.array_equal(a["d2x"], b["d2x"])
+    assert np.array_equal(a["dvx"], -b["dvx"])
+    z = oracle.o1(np.zeros(10), 10 ** np.linspace(-6, 5, 10), precision="long", second=True)
+    assert np.all(z["dvx"] == 0)
+    assert np.all(a["d2x"] > 0) and np.all(a["d2v"] > 0)
+
+
+def test_second_derivatives_o1_against_dense():
+    """The method's second derivatives at 128 bins against the dense quadrature; the plain
+    combinations cancel to about 1/(2 x^2) at large x, so the bound scales with the terms."""
+    v, x = W.full_domain(1000, seed=123)
+    d = oracle.dense(v, x, second=True)
+    lo = oracle.o1(v, x, precision="long", second=True)
+    e1 = lo["dv"] ** 2 + np.abs(d["d2v"])
+    assert np.max(np.abs(lo["d2v"] - d["d2v"]) / e1) < 1e-12
+    e2 = lo["dx"] ** 2 + np.abs(d["d2x"])
+    assert np.max(np.abs(lo["d2x"] - d["d2x"]) / e2) < 1e-12
+    e3 = np.abs(lo["dx"] * lo["dv"]) + np.abs(d["dvx"])
+    assert np.max(np.abs(lo["dvx"] - d["dvx"]) / e3) < 1e-12
+
+
+def test_second_derivatives_edge_cases():
+    v = np.array([1.0, 2.0, np.nan, 1.0, np.inf])
+    x = np.array([np.inf, 0.0, 1.0, -1.0, 1.0])
+    for out in (oracle.o1(v, x, second=True), oracle.o1(v, x, precision="long", second=True),
+                oracle.dense(v, x, second=True)):
+        for k in ("d2v", "dvx", "d2x"):
+            assert out[k][0] == 0
+            assert np.all(np.isnan(out[k][1:]))
