@@ -115,6 +115,14 @@ typedef struct kv_args {
     uint8_t* status;      /* [n] or NULL: per-pair kv_pair_status bits */
     unsigned long long* fallback_count; /* device counter or NULL: += pairs that fell back */
     void* stream;
+    /* Second derivatives of log K (Sec. 4.1, the integrands f^(n,m) with n + m = 2, over the same
+     * bins and range): [n] outs or NULL, same element type as v and x.  d2v = d2/dv2,
+     * dvx = d2/dv dx (odd in v, 0 at v = 0), d2x = d2/dx2.  When any is set, every pair runs one
+     * per thread (lanes is ignored) and logk/dv/dx, if requested, come from the same sums;
+     * grad_out does not scale them.  Edge pairs: x = +inf gives 0, the other edge inputs NaN. */
+    void* d2v;
+    void* dvx;
+    void* d2x;
 } kv_args;
 
 /* Per-pair status bits written to kv_args.status. */
@@ -131,10 +139,11 @@ int kv_fwd_bwd_ex(const kv_args* a);
 
 /* kv_fwd_bwd_ex on HOST buffers: a->v, a->x, a->logk, a->dv and a->dx are host pointers
  * (pinned with cudaHostAlloc for full speed); every other field means what it means for
- * kv_fwd_bwd_ex, except that grad_out, status and fallback_count must be NULL.  The call copies
- * the inputs to the device, computes and copies the outputs back, pipelined in chunks of up to
- * 2^20 pairs rotating over a->stream and two internal streams, and returns when the host outputs
- * are complete.  Device staging memory is allocated and freed on the stream inside the call. */
+ * kv_fwd_bwd_ex, except that grad_out, status, fallback_count and the second-derivative outputs
+ * must be NULL (else KV_ERR_ARG).  The call copies the inputs to the device, computes and copies
+ * the outputs back, pipelined in chunks of up to 2^19 pairs rotating over a->stream and three
+ * internal streams, and returns when the host outputs are complete.  Device staging memory is
+ * allocated and freed on the stream inside the call. */
 int kv_fwd_bwd_host(const kv_args* a);
 
 /* ------------------------------------------------------------------ building blocks */
@@ -147,6 +156,17 @@ int kv_bracket(const void* v, const void* x, double* t0, double* tp, double* t1,
 /* The backward epilogue on its own: grad_v = grad_out * dv, grad_x = grad_out * dx. */
 int kv_grad(const void* grad_out, const void* dv, const void* dx, void* grad_v, void* grad_x,
             int64_t n, int dtype, void* stream);
+
+/* The epilogue of the second backward pass (the backward of kv_grad's outputs
+ * g_v = go * dv, g_x = go * dx with incoming gradients gg_v, gg_x):
+ *   out_v  = go * (gg_v * d2v + gg_x * dvx)
+ *   out_x  = go * (gg_v * dvx + gg_x * d2x)
+ *   out_go = gg_v * dv + gg_x * dx
+ * All pointers are [n] device arrays of the dtype's element type (gg_v or gg_x may be NULL for
+ * zero); outputs may be NULL individually.  Errors as for kv_grad. */
+int kv_grad2(const void* go, const void* gg_v, const void* gg_x, const void* dv, const void* dx,
+             const void* d2v, const void* dvx, const void* d2x, void* out_v, void* out_x,
+             void* out_go, int64_t n, int dtype, void* stream);
 
 /* Deterministic sum of n elements (dtype's element type) into *out (one double, device memory).
  * Used for the log-likelihood sum_i log K(v_i, x_i).  Scratch memory for the per-block partial

@@ -27,7 +27,7 @@ KV_PAIR_OK, KV_PAIR_EDGE, KV_PAIR_FALLBACK, KV_PAIR_RANGE_CAP = 0, 1, 2, 4
 #: every function include/kv.h declares
 EXPORTED = [
     "kv_log", "kv_log_dv", "kv_log_dx", "kv_fwd_bwd", "kv_fwd_bwd_ex", "kv_fwd_bwd_host",
-    "kv_bracket", "kv_grad", "kv_sum", "kv_sum_noalloc", "kv_mlp_create", "kv_mlp_free", "kv_mlp_save",
+    "kv_bracket", "kv_grad", "kv_grad2", "kv_sum", "kv_sum_noalloc", "kv_mlp_create", "kv_mlp_free", "kv_mlp_save",
     "kv_mlp_load", "kv_mlp_get_params", "kv_mlp_set_params", "kv_mlp_train",
     "kv_mlp_loss_grad", "kv_mlp_predict", "kv_launch_count", "kv_strerror",
     "kv_last_cuda_error",
@@ -42,6 +42,7 @@ class KvArgs(ctypes.Structure):
         ("bracket", ctypes.c_int), ("log_eps", ctypes.c_double), ("max_iter", ctypes.c_int),
         ("lanes", ctypes.c_int), ("mlp", ctypes.c_void_p), ("status", ctypes.c_void_p),
         ("fallback_count", ctypes.c_void_p), ("stream", ctypes.c_void_p),
+        ("d2v", ctypes.c_void_p), ("dvx", ctypes.c_void_p), ("d2x", ctypes.c_void_p),
     ]
 
 
@@ -66,6 +67,7 @@ def _declare(lib):
         "kv_fwd_bwd_host": [ctypes.POINTER(KvArgs)],
         "kv_bracket": [P, P, P, P, P, P, I64, I, D, I, P],
         "kv_grad": [P, P, P, P, P, I64, I, P],
+        "kv_grad2": [P, P, P, P, P, P, P, P, P, P, P, I64, I, P],
         "kv_sum": [P, I64, I, P, P],
         "kv_sum_noalloc": [P, I64, I, P, P],
         "kv_mlp_create": [ctypes.c_uint64, ctypes.POINTER(P)],

@@ -71,6 +71,7 @@ __device__ __forceinline__ T lane_sum(T a)
 
 struct BinsD {
     double v, x, t0, h, tp, s0, Lu;  // s0 = t0 - t_p, Lu = log1p(e^{-2 v t_p})
+    double e2u;                      // e^{-2 v t_p} (second derivatives only)
     int n;
 };
 
@@ -109,6 +110,7 @@ struct BinsF {
     float ap, am;   // x e^{t_p} / 2, x e^{-t_p} / 2
     float lu;       // log1p(e^{-2u})
     float ep, em;   // e^{t_p}, e^{-t_p}
+    float e2u, shp; // e^{-2u}, sinh t_p (second derivatives only)
     int n;
 };
 
@@ -354,6 +356,122 @@ __device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, fl
     S0 = lane_sum<float, L>(k0.value());
     S1 = DERIV ? lane_sum<float, L>(k1.value()) : 0.0f;
     S2 = DERIV ? lane_sum<float, L>(k2.value()) : 0.0f;
+}
+
+// ------------------------------------------------------------------ second derivatives
+// Sec. 4.1 with n + m = 2: K_vv, K_vx, K_xx integrate t^2 cosh(vt), -t cosh(t) sinh(vt) and
+// cosh^2(t) cosh(vt) times e^{-x cosh t} over the same bins.  With weights w ~ cosh(vt) e^{-x cosh t},
+// a = t tanh(vt) and c = cosh t, the log-derivatives are moments:
+//   d/dv log K = E[a],  d/dx log K = -E[c],
+//   d2/dv2 log K = E[t^2 sech^2(vt)] + Var(a),  d2/dv dx log K = -Cov(a, c),  d2/dx2 log K = Var(c).
+// The plain forms E[t^2] - E[a]^2 etc. cancel badly where the range is narrow (d2/dx2 ~ 1/(2x^2)
+// at large x against E[c]^2 ~ 1), so the sums run over the shifts about the reference point,
+// da = a - t_p tanh(u) and dc = cosh t - cosh t_p, each formed without cancellation:
+//   da = s tanh(vt) - t_p 2 (e^{-2vt} - e^{-2u}) / ((1 + e^{-2vt})(1 + e^{-2u})),
+//        with e^{-2vt} - e^{-2u} = e^{-2u} expm1(-2vs) where |2vs| < 1/2 (else the plain difference,
+//        which does not cancel there and does not turn 0 * inf into NaN when e^{-2u} underflows)
+//   dc = sinh(t_p) s + (e^{t_p}/2) phi(s) + (e^{-t_p}/2) phi(-s)   (= 2 sinh((t+t_p)/2) sinh(s/2))
+// and Var(a) = E[da^2] - E[da]^2 etc., where E[da], E[dc] are small near the peak.
+template <typename T>
+struct Sums2 {
+    T s0, a1, a2, c1, c2, x, q;  // sum w, w da, w da^2, w dc, w dc^2, w da dc, w t^2 sech^2(vt)
+};
+
+// First and second log-derivatives from the sums, with a_r = t_p tanh(u), c_r = cosh t_p (for
+// |v|; the caller applies the sign of v to dv and dvx).
+template <typename T>
+__device__ __forceinline__ void moments_finish(const Sums2<T>& m, T ar, T cr, T& dv, T& dx, T& d2v,
+                                               T& dvx, T& d2x)
+{
+    const T r = T(1) / m.s0;
+    const T ea = m.a1 * r, ec = m.c1 * r;
+    dv = ar + ea;
+    dx = -(cr + ec);
+    d2v = m.q * r + (m.a2 * r - ea * ea);
+    d2x = m.c2 * r - ec * ec;
+    dvx = ea * ec - m.x * r;
+}
+
+template <typename T, int L>
+__device__ __forceinline__ Sums2<T> lane_sums2(const KahanSum<T> (&k)[7])
+{
+    Sums2<T> m;
+    m.s0 = lane_sum<T, L>(k[0].value());
+    m.a1 = lane_sum<T, L>(k[1].value());
+    m.a2 = lane_sum<T, L>(k[2].value());
+    m.c1 = lane_sum<T, L>(k[3].value());
+    m.c2 = lane_sum<T, L>(k[4].value());
+    m.x = lane_sum<T, L>(k[5].value());
+    m.q = lane_sum<T, L>(k[6].value());
+    return m;
+}
+
+template <int L>
+__device__ Sums2<double> sums2_f64(const BinsD& b, int lane)
+{
+    KahanSum<double> k[7];
+    for (int j = 0; j < 7; ++j) k[j].init();
+    const double ope_u = 1.0 + b.e2u;
+    for (int m = lane; m <= b.n; m += L) {
+        const double t = b.t0 + m * b.h;
+        const double s = b.s0 + m * b.h;
+        const double e2 = exp(-2.0 * b.v * t);
+        const double dlc = b.v * s + (log1p(e2) - b.Lu);
+        const double dc = 2.0 * sinh(0.5 * (t + b.tp)) * sinh(0.5 * s);  // cosh t - cosh t_p
+        const double c = (m == 0 || m == b.n) ? 0.5 : 1.0;
+        const double w = c * exp(dlc - b.x * dc);
+        const double ope = 1.0 + e2;
+        const double th = (1.0 - e2) / ope;
+        const double vs2 = -2.0 * b.v * s;
+        const double de = fabs(vs2) < 0.5 ? b.e2u * expm1(vs2) : e2 - b.e2u;  // e^{-2vt} - e^{-2u}
+        const double da = s * th - b.tp * 2.0 * de / (ope * ope_u);
+        const double q = t * t * 4.0 * e2 / (ope * ope);
+        k[0].add(w);
+        k[1].add(w * da);
+        k[2].add(w * da * da);
+        k[3].add(w * dc);
+        k[4].add(w * dc * dc);
+        k[5].add(w * da * dc);
+        k[6].add(w * q);
+    }
+    return lane_sums2<double, L>(k);
+}
+
+template <int L>
+__device__ Sums2<float> sums2_f32(const BinsF& b, int lane)
+{
+    const BinsK kk = bins_k(b);
+    KahanSum<float> k[7];
+    for (int j = 0; j < 7; ++j) k[j].init();
+    const float rope_u = 1.0f / (1.0f + b.e2u);
+    float mf = (float)lane;
+    for (int m = lane; m <= b.n; m += L, mf += (float)L) {
+        const float s = fmaf(mf, b.h, b.s0);
+        float php, phm, es, ems;
+        phi_pair(s, php, phm, es, ems);
+        const float vt = fmaf(b.v, s, b.u);
+        const float e2 = ex2_approx(-2.0f * LOG2E_F * vt);
+        const float ope = 1.0f + e2;
+        const float dg = fmaf(kk.c1, s, lg2_approx(ope)) - fmaf(kk.ap, php, fmaf(kk.am, phm, kk.lu));
+        const float c = (m == 0 || m == b.n) ? 0.5f : 1.0f;
+        const float w = c * ex2_approx(dg);
+        const float rope = 1.0f / ope;
+        const float th = vt < TANH_SERIES_MAX ? tanh_small(vt) : (1.0f - e2) * rope;
+        const float t = b.tp + s;
+        const float vs2 = -2.0f * b.v * s;
+        const float de = fabsf(vs2) < 0.5f ? b.e2u * expm1f(vs2) : e2 - b.e2u;  // e^{-2vt} - e^{-2u}
+        const float da = s * th - b.tp * 2.0f * de * rope * rope_u;
+        const float dc = fmaf(b.shp, s, 0.5f * fmaf(b.ep, php, b.em * phm));
+        const float q = t * t * 4.0f * e2 * rope * rope;
+        k[0].add(w);
+        k[1].add(w * da);
+        k[2].add(w * da * da);
+        k[3].add(w * dc);
+        k[4].add(w * dc * dc);
+        k[5].add(w * da * dc);
+        k[6].add(w * q);
+    }
+    return lane_sums2<float, L>(k);
 }
 
 }  // namespace kvd

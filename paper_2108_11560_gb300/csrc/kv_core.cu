@@ -70,6 +70,9 @@ struct KParams {
     void* dx;
     const void* go;
     uint8_t* status;
+    void* d2v;  // second derivatives (may be NULL)
+    void* dvx;
+    void* d2x;
     int64_t n;
     int bins;
     double log_eps;
@@ -125,8 +128,24 @@ __device__ __forceinline__ void store_outputs(const KParams& p, int64_t i, doubl
     if (p.status) p.status[i] = st;
 }
 
-// FP64 plain path: the paper's bracket and bins, all in double.
-template <int L, bool DERIV>
+// Second derivatives of an edge pair (x = +inf: all 0; other edge inputs: NaN).
+__device__ __forceinline__ void edge_second(double x, double& d2v, double& dvx, double& d2x)
+{
+    d2v = dvx = d2x = (isinf(x) && x > 0.0) ? 0.0 : nan("");
+}
+
+template <typename T>
+__device__ __forceinline__ void store_second(const KParams& p, int64_t i, double d2v, double dvx, double d2x)
+{
+    if (p.d2v) ((T*)p.d2v)[i] = (T)d2v;
+    if (p.dvx) ((T*)p.dvx)[i] = (T)dvx;
+    if (p.d2x) ((T*)p.d2x)[i] = (T)d2x;
+}
+
+// FP64 plain path: the paper's bracket and bins, all in double.  With D2 (L = 1 only) the bins
+// also give the second derivatives (sums2_f64), and the first derivatives come from the same
+// shifted sums.
+template <int L, bool DERIV, bool D2 = false>
 __global__ void __launch_bounds__(kBlock) kv_f64_kernel(KParams p)
 {
     const int lane = threadIdx.x % L;
@@ -153,6 +172,28 @@ __global__ void __launch_bounds__(kBlock) kv_f64_kernel(KParams p)
         b.s0 = br.t0 - br.tp;
         b.Lu = log1p(exp(-2.0 * va * br.tp));
         b.n = p.bins;
+        if constexpr (D2) {
+            b.e2u = exp(-2.0 * va * br.tp);
+            const Sums2<double> m = sums2_f64<L>(b, lane);
+            if (active) {
+                double d2v, dvx, d2x;
+                uint8_t st = KV_PAIR_OK;
+                if (edge) {
+                    edge_second(x, d2v, dvx, d2x);
+                    st = KV_PAIR_EDGE;
+                } else {
+                    const double ar = br.tp * ((1.0 - b.e2u) / (1.0 + b.e2u));
+                    moments_finish<double>(m, ar, cosh(br.tp), dv, dx, d2v, dvx, d2x);
+                    lk = br.G + log(b.h) + log(m.s0);
+                    dv = v == 0.0 ? 0.0 : copysign(dv, v);
+                    dvx = v == 0.0 ? 0.0 : copysign(1.0, v) * dvx;
+                    if (br.capped) st = KV_PAIR_RANGE_CAP;
+                }
+                store_outputs<double>(p, i, lk, dv, dx, st);
+                store_second<double>(p, i, d2v, dvx, d2x);
+            }
+            continue;
+        }
         double S0, S1, S2;
         sums_f64<L, DERIV>(b, lane, S0, S1, S2);
         if (active && lane == 0) {
@@ -172,7 +213,8 @@ __global__ void __launch_bounds__(kBlock) kv_f64_kernel(KParams p)
 }
 
 // Mixed path with the plain FP64 bracket: FP64 peak, offset and per-pair constants, FP32 bins.
-template <int L, bool DERIV>
+// D2 (L = 1 only): second derivatives from the shifted FP32 sums (sums2_f32).
+template <int L, bool DERIV, bool D2 = false>
 __global__ void __launch_bounds__(kBlock) kv_mixed_kernel(KParams p)
 {
     const int lane = threadIdx.x % L;
@@ -206,6 +248,34 @@ __global__ void __launch_bounds__(kBlock) kv_mixed_kernel(KParams p)
         b.ep = (float)ep;
         b.em = (float)em;
         b.n = p.bins;
+        if constexpr (D2) {
+            const double e2u = exp(-2.0 * u);
+            b.e2u = (float)e2u;
+            b.shp = (float)sinh(br.tp);
+            const Sums2<float> m = sums2_f32<L>(b, lane);
+            if (active) {
+                double d2v, dvx, d2x;
+                uint8_t st = KV_PAIR_OK;
+                if (edge) {
+                    edge_second(x, d2v, dvx, d2x);
+                    st = KV_PAIR_EDGE;
+                } else {
+                    float fdv, fdx, fd2v, fdvx, fd2x;
+                    moments_finish<float>(m, (float)(br.tp * ((1.0 - e2u) / (1.0 + e2u))), (float)cosh(br.tp),
+                                          fdv, fdx, fd2v, fdvx, fd2x);
+                    lk = br.G + (double)logf(b.h * m.s0);
+                    dv = v == 0.0 ? 0.0 : copysign((double)fdv, v);
+                    dx = fdx;
+                    d2v = fd2v;
+                    dvx = v == 0.0 ? 0.0 : copysign(1.0, v) * (double)fdvx;
+                    d2x = fd2x;
+                    if (br.capped) st = KV_PAIR_RANGE_CAP;
+                }
+                store_outputs<float>(p, i, lk, dv, dx, st);
+                store_second<float>(p, i, d2v, dvx, d2x);
+            }
+            continue;
+        }
         float S0, S1, S2;
         sums_f32<L, DERIV>(b, lane, S0, S1, S2);
         if (active && lane == 0) {
@@ -258,6 +328,29 @@ __global__ void kv_grad_kernel(const T* go, const T* dv, const T* dx, T* gv, T* 
         T g = go[i];
         if (gv) gv[i] = g * dv[i];
         if (gx) gx[i] = g * dx[i];
+    }
+}
+
+// The second backward pass's epilogue (the backward of g_v = go dv, g_x = go dx).
+template <typename T>
+struct Grad2Args {
+    const T *go, *ggv, *ggx, *dv, *dx, *d2v, *dvx, *d2x;
+    T *ov, *ox, *ogo;
+    int64_t n;
+};
+
+template <typename T>
+__global__ void kv_grad2_kernel(Grad2Args<T> a)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const T gv = a.ggv ? a.ggv[i] : T(0), gx = a.ggx ? a.ggx[i] : T(0);
+        if (a.ov || a.ox) {
+            const T go = a.go[i], dvx = a.dvx[i];
+            if (a.ov) a.ov[i] = go * (gv * a.d2v[i] + gx * dvx);
+            if (a.ox) a.ox[i] = go * (gv * dvx + gx * a.d2x[i]);
+        }
+        if (a.ogo) a.ogo[i] = gv * a.dv[i] + gx * a.dx[i];
     }
 }
 
@@ -320,6 +413,13 @@ int launch_pairs(K kernel, const KParams& p, int lanes, cudaStream_t s)
     return KV_OK;
 }
 
+// Second derivatives: one pair per thread.
+int dispatch_second(const KParams& p, int dtype, cudaStream_t s)
+{
+    if (dtype == KV_F64) return launch_pairs(kv_f64_kernel<1, true, true>, p, 1, s);
+    return launch_pairs(kv_mixed_kernel<1, true, true>, p, 1, s);
+}
+
 template <int L>
 int dispatch_deriv(const KParams& p, int dtype, bool deriv, cudaStream_t s)
 {
@@ -345,7 +445,7 @@ int validate(const kv_args* a, int* bins, double* log_eps, int* max_iter, int* l
     if (a->dtype != KV_F64 && a->dtype != KV_MIXED) return KV_ERR_DTYPE;
     if (a->n < 0) return KV_ERR_SIZE;
     if (a->n > 0 && (!a->v || !a->x)) return KV_ERR_NULL;
-    if (a->n > 0 && !a->logk && !a->dv && !a->dx) return KV_ERR_NULL;
+    if (a->n > 0 && !a->logk && !a->dv && !a->dx && !a->d2v && !a->dvx && !a->d2x) return KV_ERR_NULL;
     *bins = a->bins == 0 ? (a->dtype == KV_F64 ? 128 : 40) : a->bins;
     if (*bins < 1 || *bins > KV_MAX_BINS) return KV_ERR_BINS;
     *log_eps = a->log_eps == 0.0 ? (a->dtype == KV_F64 ? -52.0 * kvd::LN2_D : -20.0) : a->log_eps;
@@ -361,7 +461,7 @@ int validate(const kv_args* a, int* bins, double* log_eps, int* max_iter, int* l
         if (!a->mlp) return KV_ERR_HANDLE;
     }
     size_t es = kvh::elem_size(a->dtype);
-    const void* ptrs[6] = {a->v, a->x, a->logk, a->dv, a->dx, a->grad_out};
+    const void* ptrs[9] = {a->v, a->x, a->logk, a->dv, a->dx, a->grad_out, a->d2v, a->dvx, a->d2x};
     for (const void* q : ptrs)
         if (q && !kvh::aligned(q, es)) return KV_ERR_ALIGN;
     return KV_OK;
@@ -391,12 +491,16 @@ int kvh::fwd_bwd_ex(const kv_args* a, uint32_t* scratch)
     p.dx = a->dx;
     p.go = a->grad_out;
     p.status = a->status;
+    p.d2v = a->d2v;
+    p.dvx = a->dvx;
+    p.d2x = a->d2x;
     p.n = a->n;
     p.bins = bins;
     p.log_eps = log_eps;
     p.max_iter = max_iter;
     const bool deriv = a->dv || a->dx;
     cudaStream_t s = (cudaStream_t)a->stream;
+    if (a->d2v || a->dvx || a->d2x) return dispatch_second(p, a->dtype, s);
     switch (lanes) {
         case 1: return dispatch_deriv<1>(p, a->dtype, deriv, s);
         case 2: return dispatch_deriv<2>(p, a->dtype, deriv, s);
@@ -513,6 +617,46 @@ int kv_grad(const void* grad_out, const void* dv, const void* dx, void* grad_v, 
     return KV_OK;
 }
 
+}  // extern "C"
+
+template <typename T>
+static void launch_grad2(const void* go, const void* ggv, const void* ggx, const void* dv,
+                         const void* dx, const void* d2v, const void* dvx, const void* d2x,
+                         void* ov, void* ox, void* ogo, int64_t n, int grid, cudaStream_t s)
+{
+    Grad2Args<T> a{(const T*)go, (const T*)ggv, (const T*)ggx, (const T*)dv, (const T*)dx,
+                   (const T*)d2v, (const T*)dvx, (const T*)d2x, (T*)ov, (T*)ox, (T*)ogo, n};
+    kv_grad2_kernel<T><<<grid, 256, 0, s>>>(a);
+}
+
+extern "C" {
+
+int kv_grad2(const void* go, const void* gg_v, const void* gg_x, const void* dv, const void* dx,
+             const void* d2v, const void* dvx, const void* d2x, void* out_v, void* out_x,
+             void* out_go, int64_t n, int dtype, void* stream)
+{
+    if (dtype != KV_F64 && dtype != KV_MIXED) return KV_ERR_DTYPE;
+    if (n < 0) return KV_ERR_SIZE;
+    if (n == 0) return KV_OK;
+    if (!out_v && !out_x && !out_go) return KV_ERR_NULL;
+    if ((out_v || out_x) && (!go || !d2v || !dvx || !d2x)) return KV_ERR_NULL;
+    if (out_go && (!dv || !dx)) return KV_ERR_NULL;
+    size_t es = kvh::elem_size(dtype);
+    const void* ptrs[11] = {go, gg_v, gg_x, dv, dx, d2v, dvx, d2x, out_v, out_x, out_go};
+    for (const void* q : ptrs)
+        if (q && !kvh::aligned(q, es)) return KV_ERR_ALIGN;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t need = (n + 255) / 256;
+    int64_t cap = (int64_t)kvh::sm_count() * 16;
+    int grid = (int)(need < cap ? need : cap);
+    if (dtype == KV_F64)
+        launch_grad2<double>(go, gg_v, gg_x, dv, dx, d2v, dvx, d2x, out_v, out_x, out_go, n, grid, s);
+    else
+        launch_grad2<float>(go, gg_v, gg_x, dv, dx, d2v, dvx, d2x, out_v, out_x, out_go, n, grid, s);
+    KV_LAUNCH_CHECK();
+    return KV_OK;
+}
+
 // Number of partial sums for n elements: a function of n only, so results are reproducible.
 static int sum_blocks(int64_t n)
 {
@@ -560,7 +704,7 @@ int kv_sum(const void* a, int64_t n, int dtype, double* out, void* stream)
 int kv_fwd_bwd_host(const kv_args* h)
 {
     if (!h) return KV_ERR_NULL;
-    if (h->grad_out || h->status || h->fallback_count) return KV_ERR_ARG;
+    if (h->grad_out || h->status || h->fallback_count || h->d2v || h->dvx || h->d2x) return KV_ERR_ARG;
     int bins_, max_iter_, lanes_;
     double log_eps_;
     int rc = validate(h, &bins_, &log_eps_, &max_iter_, &lanes_);

@@ -308,7 +308,8 @@ __device__ __forceinline__ PeakConst peak_constants(float v, float x, float tp, 
     df u = two_prod(v, tr.hi);
     u = fast_two_sum(u.hi, fmaf(v, tr.lo, u.lo));
     // log1p(e^{-2u}) in [0, ln 2] from the approximate 2^x and log2 (absolute error ~2e-7)
-    const float lu = lg2_approx(1.0f + ex2_approx(-2.0f * LOG2E_F * u.hi)) * LN2_F;
+    const float e2u = ex2_approx(-2.0f * LOG2E_F * u.hi);
+    const float lu = lg2_approx(1.0f + e2u) * LN2_F;
     const df ch = df_mul_f(df_add_fast(E, Ei), 0.5f * x);  // x cosh t_r
     const df sh = df_mul_f(df_sub_fast(E, Ei), 0.5f * x);  // x sinh t_r
     c.G = df_sub_fast(df_add_fast(df_add_fast(u, df_make(lu)), df_neg(df_ln2())), ch);
@@ -322,6 +323,9 @@ __device__ __forceinline__ PeakConst peak_constants(float v, float x, float tp, 
     c.b.lu = lu;
     c.b.ep = E.hi;
     c.b.em = Ei.hi;
+    c.b.e2u = e2u;
+    const df shr = df_sub_fast(E, Ei);  // 2 sinh t_r
+    c.b.shp = 0.5f * (shr.hi + shr.lo);
     return c;
 }
 
@@ -342,6 +346,9 @@ struct MlpPathParams {
     float* dx;
     const float* go;
     uint8_t* status;
+    float* d2v;  // second derivatives (may be NULL)
+    float* dvx;
+    float* d2x;
     int64_t n;
     int bins;
     float inv_bins;  // 1 / bins
@@ -525,7 +532,7 @@ constexpr uint32_t kTmemCols = 64;
 // 3 on the tensor cores as well measured slower: the second MMA round trip per tile costs more
 // than the 128 FMAs it saves.)  A wait that does not finish within its limit sends the CTA's
 // remaining pairs to the fallback list (correct, slower) instead of hanging.
-template <bool DERIV>
+template <bool DERIV, bool D2 = false>
 __global__ void __launch_bounds__(kMlpBlock, 8) kv_mlp_tc_kernel(MlpPathParams p)
 {
     __shared__ __align__(1024) TcSmem sm;
@@ -643,7 +650,23 @@ __global__ void __launch_bounds__(kMlpBlock, 8) kv_mlp_tc_kernel(MlpPathParams p
         c.b.h = (t1 - t0) * p.inv_bins;
         c.b.n = p.bins;
         float S0, S1, S2;
-        sums_f32<1, DERIV, true>(c.b, 0, S0, S1, S2);
+        float d2v = 0.0f, dvx = 0.0f, d2x = 0.0f;
+        if constexpr (D2) {
+            // second derivatives (and the first ones) from the shifted sums
+            const Sums2<float> m = sums2_f32<1>(c.b, 0);
+            S0 = m.s0;
+            const float ar = tr * (c.b.u < TANH_SERIES_MAX ? tanh_small(c.b.u)
+                                                            : (1.0f - c.b.e2u) / (1.0f + c.b.e2u));
+            float fdv, fdx;
+            moments_finish<float>(m, ar, 0.5f * (c.b.ep + c.b.em), fdv, fdx, d2v, dvx, d2x);
+            S1 = fdv * S0;
+            S2 = -fdx * S0;
+            if (v == 0.0f) dvx = 0.0f;
+            if (v < 0.0f) dvx = -dvx;
+            if (edge) d2v = dvx = d2x = (isinf(x) && x > 0.0f) ? 0.0f : nanf("");
+        } else {
+            sums_f32<1, DERIV, true>(c.b, 0, S0, S1, S2);
+        }
         if (regular && ok) {
             // log(h S0) from the approximate log2 (absolute error about 1e-7)
             df L = df_add(c.G, df_make(lg2_approx(c.b.h * S0) * LN2_F));
@@ -662,6 +685,11 @@ __global__ void __launch_bounds__(kMlpBlock, 8) kv_mlp_tc_kernel(MlpPathParams p
             if (p.dv) p.dv[i] = dv;
             if (p.dx) p.dx[i] = dx;
             if (p.status) p.status[i] = edge ? KV_PAIR_EDGE : KV_PAIR_OK;
+            if constexpr (D2) {
+                if (p.d2v) p.d2v[i] = d2v;
+                if (p.dvx) p.dvx[i] = dvx;
+                if (p.d2x) p.d2x[i] = d2x;
+            }
         }
     }
     if (aborted) {
@@ -725,7 +753,7 @@ struct FallbackParams {
 
 // The pairs whose learned bracket failed its check: the plain FP64 bracket (Algorithms 1-3) and
 // FP64 constants, then the same FP32 bins.
-template <bool DERIV>
+template <bool DERIV, bool D2 = false>
 __global__ void __launch_bounds__(kMlpBlock) kv_fallback_kernel(FallbackParams f)
 {
     const MlpPathParams& p = f.p;
@@ -754,7 +782,25 @@ __global__ void __launch_bounds__(kMlpBlock) kv_fallback_kernel(FallbackParams f
         b.em = (float)em;
         b.n = p.bins;
         float S0, S1, S2;
-        sums_f32<1, DERIV>(b, 0, S0, S1, S2);
+        if constexpr (D2) {
+            const double e2u = exp(-2.0 * u);
+            b.e2u = (float)e2u;
+            b.shp = (float)sinh(br.tp);
+            const Sums2<float> m = sums2_f32<1>(b, 0);
+            float fdv, fdx, d2v, dvx, d2x;
+            moments_finish<float>(m, (float)(br.tp * ((1.0 - e2u) / (1.0 + e2u))), (float)cosh(br.tp), fdv,
+                                  fdx, d2v, dvx, d2x);
+            S0 = m.s0;
+            S1 = fdv * S0;
+            S2 = -fdx * S0;
+            if (v == 0.0) dvx = 0.0f;
+            if (v < 0.0) dvx = -dvx;
+            if (p.d2v) p.d2v[i] = d2v;
+            if (p.dvx) p.dvx[i] = dvx;
+            if (p.d2x) p.d2x[i] = d2x;
+        } else {
+            sums_f32<1, DERIV>(b, 0, S0, S1, S2);
+        }
         double lk = br.G + (double)logf(b.h * S0);
         float r = 1.0f / S0;
         double dv = DERIV ? copysign((double)(S1 * r), v) : 0.0;
@@ -1041,6 +1087,9 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
     p.dx = (float*)a->dx;
     p.go = (const float*)a->grad_out;
     p.status = a->status;
+    p.d2v = (float*)a->d2v;
+    p.dvx = (float*)a->dvx;
+    p.d2x = (float*)a->d2x;
     p.n = a->n;
     rc = fill_mlp_const(a->mlp, (cudaStream_t)a->stream, &p.wc);
     if (rc != KV_OK) return rc;
@@ -1056,14 +1105,18 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
     p.fb_count = scratch;
     p.fb_list = scratch + 32;
     cudaError_t e = cudaMemsetAsync(p.fb_count, 0, sizeof(uint32_t), s);
-    const bool deriv = a->dv || a->dx;
+    const bool second = a->d2v || a->dvx || a->d2x;
+    const bool deriv = a->dv || a->dx || second;
     if (e == cudaSuccess) {
         // persistent grid; at most 8 CTAs per SM so that their 64 TMEM columns each fit in 512
-        const int per_sm = deriv ? tc_blocks_per_sm(kv_mlp_tc_kernel<true>) : tc_blocks_per_sm(kv_mlp_tc_kernel<false>);
+        const int per_sm = second  ? tc_blocks_per_sm(kv_mlp_tc_kernel<true, true>)
+                           : deriv ? tc_blocks_per_sm(kv_mlp_tc_kernel<true>)
+                                   : tc_blocks_per_sm(kv_mlp_tc_kernel<false>);
         int64_t need = (a->n + kMlpBlock - 1) / kMlpBlock;
         int64_t cap = (int64_t)sm_count() * per_sm;
         int grid = (int)(need < cap ? need : cap);
-        if (deriv) kv_mlp_tc_kernel<true><<<grid, kMlpBlock, 0, s>>>(p);
+        if (second) kv_mlp_tc_kernel<true, true><<<grid, kMlpBlock, 0, s>>>(p);
+        else if (deriv) kv_mlp_tc_kernel<true><<<grid, kMlpBlock, 0, s>>>(p);
         else kv_mlp_tc_kernel<false><<<grid, kMlpBlock, 0, s>>>(p);
         note_launch();
         e = cudaGetLastError();
@@ -1075,7 +1128,8 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
         f.max_iter = max_iter;
         f.fallback_total = a->fallback_count;
         int grid = sm_count() * 4;
-        if (deriv) kv_fallback_kernel<true><<<grid, kMlpBlock, 0, s>>>(f);
+        if (second) kv_fallback_kernel<true, true><<<grid, kMlpBlock, 0, s>>>(f);
+        else if (deriv) kv_fallback_kernel<true><<<grid, kMlpBlock, 0, s>>>(f);
         else kv_fallback_kernel<false><<<grid, kMlpBlock, 0, s>>>(f);
         note_launch();
         e = cudaGetLastError();

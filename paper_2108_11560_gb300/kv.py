@@ -86,11 +86,13 @@ def kv_fwd_bwd(v, x, bins: int = 0):
 def kv_fwd_bwd_ex(v, x, *, bins: int = 0, bracket: str = "plain", log_eps: float = 0.0,
                   max_iter: int = 0, lanes: int = 0, mlp=None, grad_out=None,
                   want=("logk", "dv", "dx"), status: bool = False, fallback_count=None,
-                  out=None):
+                  out=None, second: bool = False):
     """The general call (kv_fwd_bwd_ex).  Returns a dict with the requested outputs and, with
-    ``status=True``, the per-pair status bytes.  ``out`` may supply preallocated tensors."""
+    ``status=True``, the per-pair status bytes; ``second=True`` adds the second derivatives
+    ``d2v``, ``dvx``, ``d2x`` (Sec. 4.1, n + m = 2).  ``out`` may supply preallocated tensors."""
     v, x, dt = _check_pair(v, x)
     out = dict(out or {})
+    want = tuple(want) + (("d2v", "dvx", "d2x") if second else ())
     for k in want:
         if k not in out:
             out[k] = torch.empty_like(v)
@@ -117,6 +119,8 @@ def kv_fwd_bwd_ex(v, x, *, bins: int = 0, bracket: str = "plain", log_eps: float
     a.status = out["status"].data_ptr() if status else None
     a.fallback_count = fallback_count.data_ptr() if fallback_count is not None else None
     a.stream = _stream_ptr(v.device)
+    if second:
+        a.d2v, a.dvx, a.d2x = (out[k].data_ptr() for k in ("d2v", "dvx", "d2x"))
     N.check(N.lib().kv_fwd_bwd_ex(ctypes.byref(a)), "kv_fwd_bwd_ex")
     return out
 
@@ -184,9 +188,44 @@ def kv_sum(a):
     return out
 
 
+def kv_grad2(go, gg_v, gg_x, dv, dx, d2v, dvx, d2x):
+    """The second backward pass's epilogue: (go (gg_v d2v + gg_x dvx), go (gg_v dvx + gg_x d2x),
+    gg_v dv + gg_x dx); gg_v or gg_x may be None (zero)."""
+    dt = _dtype_code(dv)
+    outs = [torch.empty_like(dv) for _ in range(3)]
+    c = lambda t: None if t is None else t.contiguous()
+    N.check(N.lib().kv_grad2(_ptr(c(go)), _ptr(c(gg_v)), _ptr(c(gg_x)), _ptr(c(dv)), _ptr(c(dx)),
+                             _ptr(c(d2v)), _ptr(c(dvx)), _ptr(c(d2x)), *[_ptr(o) for o in outs],
+                             dv.numel(), dt, _stream_ptr(dv.device)), "kv_grad2")
+    return tuple(outs)
+
+
+class _LogBesselKGrad(torch.autograd.Function):
+    """(go * d/dv log K, go * d/dx log K) as a function of (v, x, go), so that the gradient of
+    log_besselk is itself differentiable (Hessian-vector products, double backward).  Its backward
+    asks the library for the second derivatives from the same bins and range."""
+
+    @staticmethod
+    def forward(ctx, v, x, go, dv, dx, bins, bracket, mlp):
+        ctx.save_for_backward(v, x, go, dv, dx)
+        ctx.cfg = (bins, bracket, mlp)
+        return kv_grad(go.contiguous(), dv, dx)
+
+    @staticmethod
+    @torch.autograd.function.once_differentiable
+    def backward(ctx, gg_v, gg_x):
+        v, x, go, dv, dx = ctx.saved_tensors
+        bins, bracket, mlp = ctx.cfg
+        s = kv_fwd_bwd_ex(v.detach(), x.detach(), bins=bins, bracket=bracket, mlp=mlp, want=(),
+                          second=True)
+        ov, ox, ogo = kv_grad2(go, gg_v, gg_x, dv, dx, s["d2v"], s["dvx"], s["d2x"])
+        return ov, ox, ogo, None, None, None, None, None
+
+
 class _LogBesselK(torch.autograd.Function):
     """log K_v(x) with the fused backward: the forward keeps d/dv and d/dx from the same bins
-    and bracket; the backward multiplies them by the incoming gradient (no re-integration)."""
+    and bracket; the backward multiplies them by the incoming gradient (no re-integration), and
+    is itself differentiable once more through _LogBesselKGrad."""
 
     @staticmethod
     def forward(ctx, v, x, bins, bracket, mlp):
@@ -194,13 +233,19 @@ class _LogBesselK(torch.autograd.Function):
         want = ("logk", "dv", "dx") if (ctx.needs_input_grad[0] or ctx.needs_input_grad[1]) else ("logk",)
         out = kv_fwd_bwd_ex(vc, xc, bins=bins, bracket=bracket, mlp=mlp, want=want)
         if len(want) == 3:
-            ctx.save_for_backward(out["dv"], out["dx"])
+            # the inputs themselves (not detached copies): a double backward differentiates
+            # the gradient with respect to them
+            ctx.save_for_backward(v, x, out["dv"], out["dx"])
+        ctx.cfg = (bins, bracket, mlp)
         return out["logk"]
 
     @staticmethod
     def backward(ctx, grad):
-        dv, dx = ctx.saved_tensors
-        gv, gx = kv_grad(grad.contiguous(), dv, dx)
+        v, x, dv, dx = ctx.saved_tensors
+        if torch.is_grad_enabled():  # create_graph: keep the gradient differentiable
+            gv, gx = _LogBesselKGrad.apply(v, x, grad, dv, dx, *ctx.cfg)
+        else:
+            gv, gx = kv_grad(grad.contiguous(), dv, dx)
         return gv, gx, None, None, None
 
 

@@ -81,3 +81,25 @@ def test_host_side_argument_errors(lib):
     a.bins = 0
     a.status = 256
     assert lib.kv_fwd_bwd_host(ctypes.byref(a)) == -7
+
+
+def test_second_derivative_argument_errors(lib):
+    P = ctypes.c_void_p
+    fake = P(256)
+    a = N.KvArgs()
+    a.v = a.x = 256
+    a.n, a.bins, a.dtype = 10, 32, 0
+    assert lib.kv_fwd_bwd_ex(ctypes.byref(a)) == -1  # no output at all
+    a.d2x = 256 + 4  # misaligned for double
+    assert lib.kv_fwd_bwd_ex(ctypes.byref(a)) == -5
+    # the host-buffer call takes no second-derivative outputs
+    h = N.KvArgs()
+    h.v = h.x = h.logk = 256
+    h.n, h.bins, h.dtype = 5, 32, 0
+    h.dvx = 256
+    assert lib.kv_fwd_bwd_host(ctypes.byref(h)) == -7
+    # second backward epilogue
+    assert lib.kv_grad2(fake, fake, fake, fake, fake, fake, fake, fake, None, None, None, 5, 0, None) == -1
+    assert lib.kv_grad2(None, fake, fake, fake, fake, fake, fake, fake, fake, None, None, 5, 0, None) == -1
+    assert lib.kv_grad2(fake, fake, fake, fake, fake, fake, fake, fake, fake, None, None, 5, 9, None) == -4
+    assert lib.kv_grad2(fake, fake, fake, fake, fake, fake, fake, fake, fake, None, None, -1, 0, None) == -2
