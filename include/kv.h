@@ -52,8 +52,14 @@ enum kv_bracket_mode {
     /* Algorithms 1-3 in FP64 (Sec. 2.2-2.3). */
     KV_BRACKET_PLAIN = 0,
     /* A 2-64-64-2 MLP on (v, log x) predicts (t0, t1); each pair checks g at both ends and falls
-     * back to KV_BRACKET_PLAIN when the check fails.  KV_MIXED only.  Needs kv_args.mlp. */
-    KV_BRACKET_MLP = 1
+     * back to the plain bracket (in FP32, then FP64) when the check fails.  KV_MIXED only.
+     * Needs kv_args.mlp. */
+    KV_BRACKET_MLP = 1,
+    /* Algorithms 1-3 in FP32 (the 32-bit variant of Sec. 4.2), with the range functions evaluated
+     * as cancellation-free differences about a grid point next to the peak and the offset as a
+     * float-float (no FP64 on the path); pairs whose FP32 range is not finite fall back to FP64.
+     * KV_MIXED only. */
+    KV_BRACKET_PLAIN_F32 = 2
 };
 
 /* Status codes. */

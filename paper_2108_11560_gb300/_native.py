@@ -18,6 +18,7 @@ KV_F64 = 0
 KV_MIXED = 1
 KV_BRACKET_PLAIN = 0
 KV_BRACKET_MLP = 1
+KV_BRACKET_PLAIN_F32 = 2
 KV_OK = 0
 KV_MAX_BINS = 4096
 KV_MLP_NPARAMS = 4482

@@ -1,0 +1,156 @@
+// FP32 range finding for one (v, x) pair: Algorithms 1-3 (Sec. 2.1-2.3) in single precision, the
+// bracket of the paper's 32-bit variant (Sec. 4.2).
+//
+// The searches are those of kv_bracket.cuh (same readings: FindZero keeps the end where F < 0,
+// takes the bisection point and the clipped Newton point each iteration and returns the negative
+// end after exactly max_iter iterations; FindRange doubles from m = 0).  What changes is how the
+// functions are evaluated so that FP32 suffices:
+//  * the peak search works on g'(t) = v tanh(vt) - x sinh t and g''(t) directly (their zero and
+//    sign need only FP32 relative accuracy of the two terms);
+//  * the range searches work on h(t) = g(t) - g(t_r) - log eps through the cancellation-free
+//    difference of kv_bins.cuh about a reference point t_r next to the peak (the caller supplies
+//    the per-pair constants at t_r), so h is accurate to a few 1e-7 of its terms instead of
+//    losing |g| 2^-24 to the subtraction of two large numbers.  g(t_r) <= g(t_p) by at most a
+//    fraction of a nat (t_r is within ln2/256 of the FP32 peak), which widens the range by that
+//    much.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "kv_bins.cuh"
+
+namespace kvd {
+
+constexpr int KV_RANGE_CAP_F32 = 11;
+
+// sinh t and cosh t for t >= 0 in FP32: a short series below 1/2 (where e^t - e^-t cancels),
+// ex2 and its reciprocal above.
+__device__ __forceinline__ void sinh_cosh_f32(float t, float& sh, float& ch)
+{
+    const float et = ex2_approx(t * LOG2E_F), eti = rcp_approx(et);
+    const float z = t * t;
+    const float ss = t * fmaf(z, fmaf(z, fmaf(z, 1.0f / 5040.0f, 1.0f / 120.0f), 1.0f / 6.0f), 1.0f);
+    sh = t < 0.5f ? ss : 0.5f * (et - eti);
+    ch = 0.5f * (et + eti);
+}
+
+// F = g'(t), F' = g''(t) (the peak search).
+__device__ __forceinline__ void eval_g1_g2_f32(float v, float x, float t, float& F, float& dF)
+{
+    const float vt = v * t;
+    const float e2 = ex2_approx(-2.0f * LOG2E_F * vt);
+    const float r = rcp_approx(1.0f + e2);
+    const float th = vt < TANH_SERIES_MAX ? tanh_small(vt) : (1.0f - e2) * r;
+    float sh, ch;
+    sinh_cosh_f32(t, sh, ch);
+    F = v * th - x * sh;
+    dF = v * v * (4.0f * e2 * r * r) - x * ch;
+}
+
+// F = h(t) = g(t_r + s) - g(t_r) - log eps with s = t - t_r, F' = g'(t) (the range searches).
+__device__ __forceinline__ void eval_h_f32(const BinsF& b, float le, float t, float& F, float& dF)
+{
+    const float s = t - b.tp;
+    float php, phm, es, ems;
+    phi_pair(s, php, phm, es, ems);
+    const float vt = fmaf(b.v, s, b.u);
+    const float e2 = ex2_approx(-2.0f * LOG2E_F * vt);
+    const float d = fmaf(lg2_approx(1.0f + e2), LN2_F, -b.lu);
+    F = (fmaf(b.c1, s, d) - fmaf(b.ap, php, b.am * phm)) - le;
+    // g'(t_r + s) = (v - x sinh t_r) - 2v e^{-2vt}/(1 + e^{-2vt}) - (x e^{t_r}/2)(e^s - 1) + (x e^{-t_r}/2)(e^{-s} - 1)
+    dF = b.c1 - 2.0f * b.v * e2 * rcp_approx(1.0f + e2) - b.ap * (es - 1.0f) + b.am * (ems - 1.0f);
+}
+
+template <int KIND>
+__device__ __forceinline__ void eval_F_f32(float v, float x, const BinsF& b, float le, float t, float& F,
+                                           float& dF)
+{
+    if (KIND == 0) eval_g1_g2_f32(v, x, t, F, dF);
+    else eval_h_f32(b, le, t, F, dF);
+}
+
+// Algorithm 1 in FP32; returns false when the doubling cap was hit before the sign changed.
+template <int KIND>
+__device__ __forceinline__ bool find_range_f32(float v, float x, const BinsF& b, float le, float t0,
+                                               float& t_pos, float& t_neg, float& F_neg, float& dF_neg)
+{
+    int m = 0;
+    float F, dF;
+    eval_F_f32<KIND>(v, x, b, le, t0 + 2.0f, F, dF);
+    while (m < KV_RANGE_CAP_F32 && F >= 0.0f) {
+        ++m;
+        eval_F_f32<KIND>(v, x, b, le, t0 + ldexpf(1.0f, m + 1), F, dF);
+    }
+    float lo = t0 + ldexpf(1.0f, m);
+    if (m == 0) {
+        float Flo, dFlo;
+        eval_F_f32<KIND>(v, x, b, le, lo, Flo, dFlo);
+        if (!(Flo >= 0.0f)) lo = t0;
+    }
+    t_pos = lo;
+    t_neg = t0 + ldexpf(1.0f, m + 1);
+    F_neg = F;
+    dF_neg = dF;
+    return F < 0.0f;
+}
+
+// Algorithm 2 in FP32 with a fixed trip count.
+template <int KIND>
+__device__ __forceinline__ float find_zero_f32(float v, float x, const BinsF& b, float le, float t_neg,
+                                               float t_pos, float Fa, float dFa, int max_iter)
+{
+    float a = t_neg, bb = t_pos;
+    for (int i = 0; i < max_iter; ++i) {
+        const float shrink = a + (bb - a) * 0.5f;
+        float newton = a - __fdividef(Fa, dFa);
+        if (!isfinite(newton)) newton = shrink;
+        newton = fminf(fmaxf(newton, fminf(t_neg, shrink)), fmaxf(t_neg, shrink));
+        float Fs, dFs;
+        eval_F_f32<KIND>(v, x, b, le, shrink, Fs, dFs);
+        if (Fs < 0.0f) {
+            a = shrink;
+            Fa = Fs;
+            dFa = dFs;
+        } else {
+            float Fn, dFn;
+            eval_F_f32<KIND>(v, x, b, le, newton, Fn, dFn);
+            if (Fn < 0.0f) {
+                a = newton;
+                bb = shrink;
+                Fa = Fn;
+                dFa = dFn;
+            } else {
+                bb = newton;
+            }
+        }
+    }
+    return a;
+}
+
+// Algorithm 3's peak in FP32 (0 when v^2 <= x).
+__device__ __forceinline__ float peak_alg12_f32(float v, float x, int max_iter, bool& capped)
+{
+    if (!(v * v - x > 0.0f)) return 0.0f;
+    BinsF unused;
+    float ts, te, F, dF;
+    capped |= !find_range_f32<0>(v, x, unused, 0.0f, 0.0f, ts, te, F, dF);
+    return find_zero_f32<0>(v, x, unused, 0.0f, te, ts, F, dF, max_iter);
+}
+
+// Algorithm 3's range [t0, t1] in FP32, given the peak tp and the per-pair constants b at the
+// reference point b.tp (s0, h and n of b are not used).  Returns false if the result is not a
+// finite range with 0 <= t0 <= t1.
+__device__ __forceinline__ bool range_alg12_f32(const BinsF& b, float tp, float le, int max_iter,
+                                                float& t0, float& t1, bool& capped)
+{
+    t0 = 0.0f;
+    float h0, dh0;
+    eval_h_f32(b, le, 0.0f, h0, dh0);
+    if (tp > 0.0f && h0 <= 0.0f) t0 = find_zero_f32<1>(0.0f, 0.0f, b, le, 0.0f, tp, h0, dh0, max_iter);
+    float ts, te, F, dF;
+    capped |= !find_range_f32<1>(0.0f, 0.0f, b, le, tp, ts, te, F, dF);
+    t1 = find_zero_f32<1>(0.0f, 0.0f, b, le, te, ts, F, dF, max_iter);
+    return isfinite(t0) && isfinite(t1) && t0 >= 0.0f && t1 > t0;
+}
+
+}  // namespace kvd

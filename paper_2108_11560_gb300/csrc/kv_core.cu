@@ -455,11 +455,10 @@ int validate(const kv_args* a, int* bins, double* log_eps, int* max_iter, int* l
     int L = a->lanes == 0 ? auto_lanes(a->n) : a->lanes;
     if (L != 1 && L != 2 && L != 4 && L != 8 && L != 16 && L != 32) return KV_ERR_ARG;
     *lanes = L;
-    if (a->bracket != KV_BRACKET_PLAIN && a->bracket != KV_BRACKET_MLP) return KV_ERR_ARG;
-    if (a->bracket == KV_BRACKET_MLP) {
-        if (a->dtype != KV_MIXED) return KV_ERR_DTYPE;
-        if (!a->mlp) return KV_ERR_HANDLE;
-    }
+    if (a->bracket != KV_BRACKET_PLAIN && a->bracket != KV_BRACKET_MLP && a->bracket != KV_BRACKET_PLAIN_F32)
+        return KV_ERR_ARG;
+    if (a->bracket != KV_BRACKET_PLAIN && a->dtype != KV_MIXED) return KV_ERR_DTYPE;
+    if (a->bracket == KV_BRACKET_MLP && !a->mlp) return KV_ERR_HANDLE;
     size_t es = kvh::elem_size(a->dtype);
     const void* ptrs[9] = {a->v, a->x, a->logk, a->dv, a->dx, a->grad_out, a->d2v, a->dvx, a->d2x};
     for (const void* q : ptrs)
@@ -482,7 +481,7 @@ int kvh::fwd_bwd_ex(const kv_args* a, uint32_t* scratch)
     int rc = validate(a, &bins, &log_eps, &max_iter, &lanes);
     if (rc != KV_OK) return rc;
     if (a->n == 0) return KV_OK;
-    if (a->bracket == KV_BRACKET_MLP) return kvh::launch_mlp_path(a, bins, log_eps, max_iter, scratch);
+    if (a->bracket != KV_BRACKET_PLAIN) return kvh::launch_mlp_path(a, bins, log_eps, max_iter, scratch);
     KParams p;
     p.v = a->v;
     p.x = a->x;
@@ -715,7 +714,7 @@ int kv_fwd_bwd_host(const kv_args* h)
     const int64_t chunk = n < ((int64_t)1 << KV_HOST_CHUNK_LOG2) ? n : ((int64_t)1 << KV_HOST_CHUNK_LOG2);
     const int64_t nchunks = (n + chunk - 1) / chunk;
     const int nslots = nchunks < KV_HOST_SLOTS ? (int)nchunks : KV_HOST_SLOTS;
-    const bool mlp = h->bracket == KV_BRACKET_MLP;
+    const bool mlp = h->bracket != KV_BRACKET_PLAIN;  // the paths with a fallback list
     const size_t slot_bytes = 5 * es * chunk + (mlp ? sizeof(uint32_t) * (chunk + 32) : 0);
     cudaStream_t st[KV_HOST_SLOTS] = {(cudaStream_t)h->stream};
     cudaError_t e = cudaSuccess;

@@ -29,6 +29,7 @@
 
 #include "kv_bins.cuh"
 #include "kv_bracket.cuh"
+#include "kv_bracket_f32.cuh"
 #include "kv_dfloat.cuh"
 #include "kv_internal.h"
 
@@ -523,6 +524,100 @@ __device__ __forceinline__ void sync_for_mma()
 
 constexpr uint32_t kTmemCols = 64;
 
+// The rest of a pair once its range is known (or not: ok = false), shared by the fast path and
+// the FP32 plain-bracket path.  A regular pair whose range failed goes to the fallback list and
+// runs the bins on a placeholder range (results discarded), so that every lane of the warp runs
+// the same straight-line code into the bins.  Then FP32 bins, the finish with the float-float
+// offset, and the stores.
+template <bool DERIV, bool D2>
+__device__ __forceinline__ void pair_tail(const MlpPathParams& p, int64_t i, bool active, bool edge, bool ok,
+                                          float v, float x, PeakConst& c, float t0, float t1, float lk,
+                                          float dv, float dx, uint8_t ok_status = KV_PAIR_OK)
+{
+    const float tr = c.b.tp;
+    const bool regular = active && !edge;
+    if (regular && !ok) {
+        uint32_t k = atomicAdd(p.fb_count, 1u);
+        p.fb_list[k] = (uint32_t)i;
+    }
+    if (!ok) {  // keep the bins of a failed lane finite; its results are not stored
+        t0 = fmaxf(tr - 1.0f, 0.0f);
+        t1 = tr + 1.0f;
+    }
+    __syncwarp();
+    c.b.s0 = t0 - c.b.tp;
+    c.b.h = (t1 - t0) * p.inv_bins;
+    c.b.n = p.bins;
+    float S0, S1, S2;
+    float d2v = 0.0f, dvx = 0.0f, d2x = 0.0f;
+    if constexpr (D2) {
+        // second derivatives (and the first ones) from the shifted sums
+        const Sums2<float> m = sums2_f32<1>(c.b, 0);
+        S0 = m.s0;
+        const float ar = tr * (c.b.u < TANH_SERIES_MAX ? tanh_small(c.b.u)
+                                                        : (1.0f - c.b.e2u) / (1.0f + c.b.e2u));
+        float fdv, fdx;
+        moments_finish<float>(m, ar, 0.5f * (c.b.ep + c.b.em), fdv, fdx, d2v, dvx, d2x);
+        S1 = fdv * S0;
+        S2 = -fdx * S0;
+        if (v == 0.0f) dvx = 0.0f;
+        if (v < 0.0f) dvx = -dvx;
+        if (edge) d2v = dvx = d2x = (isinf(x) && x > 0.0f) ? 0.0f : nanf("");
+    } else {
+        sums_f32<1, DERIV, true>(c.b, 0, S0, S1, S2);
+    }
+    if (regular && ok) {
+        // log(h S0) from the approximate log2 (absolute error about 1e-7)
+        df L = df_add(c.G, df_make(lg2_approx(c.b.h * S0) * LN2_F));
+        lk = L.hi + L.lo;
+        const float r = rcp_approx(S0);
+        dv = DERIV ? copysignf(S1 * r, v) : 0.0f;
+        if (v == 0.0f) dv = 0.0f;
+        dx = DERIV ? -(S2 * r) : 0.0f;
+    }
+    if (active && (edge || ok)) {
+        if (p.go) {
+            dv *= p.go[i];
+            dx *= p.go[i];
+        }
+        if (p.logk) p.logk[i] = lk;
+        if (p.dv) p.dv[i] = dv;
+        if (p.dx) p.dx[i] = dx;
+        if (p.status) p.status[i] = edge ? KV_PAIR_EDGE : ok_status;
+        if constexpr (D2) {
+            if (p.d2v) p.d2v[i] = d2v;
+            if (p.dvx) p.dvx[i] = dvx;
+            if (p.d2x) p.d2x[i] = d2x;
+        }
+    }
+}
+
+// The plain bracket in FP32 (Algorithms 1-3, kv_bracket_f32.cuh) followed by the fast path's
+// offset at a grid point, bins and finish: the paper's 32-bit variant of the whole path, one pair
+// per thread.  Pairs whose FP32 range is not a finite range go to the FP64 fallback.
+template <bool DERIV, bool D2 = false>
+__global__ void __launch_bounds__(kMlpBlock) kv_plain_f32_kernel(MlpPathParams p, int max_iter)
+{
+    const int t = threadIdx.x;
+    for (int64_t base = (int64_t)blockIdx.x * kMlpBlock; base < p.n; base += (int64_t)gridDim.x * kMlpBlock) {
+        const int64_t i = base + t;
+        const bool active = i < p.n;
+        const float v = active ? p.v[i] : 1.0f;
+        const float x = active ? p.x[i] : 1.0f;
+        float lk, dv, dx;
+        const bool edge = float_edge(v, x, lk, dv, dx);
+        const float va = edge ? 1.0f : fabsf(v);
+        const float xa = edge ? 1.0f : x;
+        bool capped = false;
+        const float tp = peak_alg12_f32(va, xa, max_iter, capped);
+        PeakConst c = peak_constants(va, xa, tp, g_exp_tab);
+        float t0, t1;
+        const bool ok = range_alg12_f32(c.b, tp, p.log_eps, max_iter, t0, t1, capped);
+        pair_tail<DERIV, D2>(p, i, active, edge, ok, v, x, c, t0, t1, lk, dv, dx,
+                             capped ? KV_PAIR_RANGE_CAP : KV_PAIR_OK);
+    }
+}
+
 // The fast path with the hidden layer on the tensor cores.  Each CTA of 128 threads takes 128
 // pairs per trip (one per thread): layer 1 on the CUDA cores writes h1 as BF16 into a K-major
 // shared tile; one elected thread issues five tcgen05.mma (M = 128, N = 64, K = 16; the fifth
@@ -636,61 +731,7 @@ __global__ void __launch_bounds__(kMlpBlock, 8) kv_mlp_tc_kernel(MlpPathParams p
         const float w1 = fmaxf(fmaxf(__expf(L1) - DELTA, 0.0f) + (tp - tr), 1e-6f * (1.0f + tr));
         float t0, t1;
         const bool ok = check_range(c.b, tr, w0, w1, p.log_eps, lo_ok, t0, t1);
-        const bool regular = active && !edge;
-        if (regular && !ok) {
-            uint32_t k = atomicAdd(p.fb_count, 1u);
-            p.fb_list[k] = (uint32_t)i;
-        }
-        if (!ok) {  // keep the bins of a failed lane finite; its results are not stored
-            t0 = fmaxf(tr - 1.0f, 0.0f);
-            t1 = tr + 1.0f;
-        }
-        __syncwarp();
-        c.b.s0 = t0 - c.b.tp;
-        c.b.h = (t1 - t0) * p.inv_bins;
-        c.b.n = p.bins;
-        float S0, S1, S2;
-        float d2v = 0.0f, dvx = 0.0f, d2x = 0.0f;
-        if constexpr (D2) {
-            // second derivatives (and the first ones) from the shifted sums
-            const Sums2<float> m = sums2_f32<1>(c.b, 0);
-            S0 = m.s0;
-            const float ar = tr * (c.b.u < TANH_SERIES_MAX ? tanh_small(c.b.u)
-                                                            : (1.0f - c.b.e2u) / (1.0f + c.b.e2u));
-            float fdv, fdx;
-            moments_finish<float>(m, ar, 0.5f * (c.b.ep + c.b.em), fdv, fdx, d2v, dvx, d2x);
-            S1 = fdv * S0;
-            S2 = -fdx * S0;
-            if (v == 0.0f) dvx = 0.0f;
-            if (v < 0.0f) dvx = -dvx;
-            if (edge) d2v = dvx = d2x = (isinf(x) && x > 0.0f) ? 0.0f : nanf("");
-        } else {
-            sums_f32<1, DERIV, true>(c.b, 0, S0, S1, S2);
-        }
-        if (regular && ok) {
-            // log(h S0) from the approximate log2 (absolute error about 1e-7)
-            df L = df_add(c.G, df_make(lg2_approx(c.b.h * S0) * LN2_F));
-            lk = L.hi + L.lo;
-            const float r = rcp_approx(S0);
-            dv = DERIV ? copysignf(S1 * r, v) : 0.0f;
-            if (v == 0.0f) dv = 0.0f;
-            dx = DERIV ? -(S2 * r) : 0.0f;
-        }
-        if (active && (edge || ok)) {
-            if (p.go) {
-                dv *= p.go[i];
-                dx *= p.go[i];
-            }
-            if (p.logk) p.logk[i] = lk;
-            if (p.dv) p.dv[i] = dv;
-            if (p.dx) p.dx[i] = dx;
-            if (p.status) p.status[i] = edge ? KV_PAIR_EDGE : KV_PAIR_OK;
-            if constexpr (D2) {
-                if (p.d2v) p.d2v[i] = d2v;
-                if (p.dvx) p.dvx[i] = dvx;
-                if (p.d2x) p.d2x[i] = d2x;
-            }
-        }
+        pair_tail<DERIV, D2>(p, i, active, edge, ok, v, x, c, t0, t1, lk, dv, dx);
     }
     if (aborted) {
         // a tensor-core wait ran out: the remaining pairs of this CTA go to the fallback pass
@@ -748,11 +789,14 @@ struct FallbackParams {
     MlpPathParams p;
     double log_eps;
     int max_iter;
+    int try_f32;  // first try the plain bracket in FP32 (the learned path's failures)
     unsigned long long* fallback_total;
 };
 
-// The pairs whose learned bracket failed its check: the plain FP64 bracket (Algorithms 1-3) and
-// FP64 constants, then the same FP32 bins.
+// The pairs whose learned bracket failed its check: the plain bracket in FP32 first (Algorithms
+// 1-3, kv_bracket_f32.cuh, with the fast path's offset and bins), and where that does not give a
+// finite range (or for the FP32 path's own failures), the plain FP64 bracket and FP64 constants,
+// then the same FP32 bins.
 template <bool DERIV, bool D2 = false>
 __global__ void __launch_bounds__(kMlpBlock) kv_fallback_kernel(FallbackParams f)
 {
@@ -762,6 +806,54 @@ __global__ void __launch_bounds__(kMlpBlock) kv_fallback_kernel(FallbackParams f
         atomicAdd(f.fallback_total, (unsigned long long)cnt);
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
         const int64_t i = p.fb_list[k];
+        if (f.try_f32) {
+            const float vf = p.v[i], xf = p.x[i];
+            const float va = fabsf(vf);
+            bool capped = false;
+            const float tp = peak_alg12_f32(va, xf, f.max_iter, capped);
+            PeakConst c = peak_constants(va, xf, tp, g_exp_tab);
+            float t0, t1;
+            if (range_alg12_f32(c.b, tp, p.log_eps, f.max_iter, t0, t1, capped)) {
+                c.b.s0 = t0 - c.b.tp;
+                c.b.h = (t1 - t0) * p.inv_bins;
+                c.b.n = p.bins;
+                float S0, S1, S2, d2v = 0.0f, dvx = 0.0f, d2x = 0.0f;
+                if constexpr (D2) {
+                    const Sums2<float> m = sums2_f32<1>(c.b, 0);
+                    S0 = m.s0;
+                    const float tr = c.b.tp;
+                    const float ar = tr * (c.b.u < TANH_SERIES_MAX ? tanh_small(c.b.u)
+                                                                    : (1.0f - c.b.e2u) / (1.0f + c.b.e2u));
+                    float fdv, fdx;
+                    moments_finish<float>(m, ar, 0.5f * (c.b.ep + c.b.em), fdv, fdx, d2v, dvx, d2x);
+                    S1 = fdv * S0;
+                    S2 = -fdx * S0;
+                    if (vf == 0.0f) dvx = 0.0f;
+                    if (vf < 0.0f) dvx = -dvx;
+                } else {
+                    sums_f32<1, DERIV>(c.b, 0, S0, S1, S2);
+                }
+                df L = df_add(c.G, df_make(lg2_approx(c.b.h * S0) * LN2_F));
+                const float r = rcp_approx(S0);
+                float dv = DERIV ? copysignf(S1 * r, vf) : 0.0f;
+                if (vf == 0.0f) dv = 0.0f;
+                float dx = DERIV ? -(S2 * r) : 0.0f;
+                if (p.go) {
+                    dv *= p.go[i];
+                    dx *= p.go[i];
+                }
+                if (p.logk) p.logk[i] = L.hi + L.lo;
+                if (p.dv) p.dv[i] = dv;
+                if (p.dx) p.dx[i] = dx;
+                if (p.status) p.status[i] = KV_PAIR_FALLBACK | (capped ? KV_PAIR_RANGE_CAP : 0);
+                if constexpr (D2) {
+                    if (p.d2v) p.d2v[i] = d2v;
+                    if (p.dvx) p.dvx[i] = dvx;
+                    if (p.d2x) p.d2x[i] = d2x;
+                }
+                continue;
+            }
+        }
         const double v = (double)p.v[i], x = (double)p.x[i];
         const double va = fabs(v);
         BracketD br = bracket_f64(va, x, f.log_eps, f.max_iter);
@@ -1077,8 +1169,10 @@ int fill_mlp_const(const kv_mlp* hc, cudaStream_t s, MlpConst* c)
 int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, uint32_t* scratch_in)
 {
     if (a->n > (int64_t)0xffffffffll) return KV_ERR_SIZE;
+    const bool f32_plain = a->bracket == KV_BRACKET_PLAIN_F32;
     MlpPathParams p;
-    int rc = mlp_view(a->mlp, &p.mlp);
+    memset(&p, 0, sizeof(p));
+    int rc = f32_plain ? KV_OK : mlp_view(a->mlp, &p.mlp);
     if (rc != KV_OK) return rc;
     p.v = (const float*)a->v;
     p.x = (const float*)a->x;
@@ -1091,7 +1185,7 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
     p.dvx = (float*)a->dvx;
     p.d2x = (float*)a->d2x;
     p.n = a->n;
-    rc = fill_mlp_const(a->mlp, (cudaStream_t)a->stream, &p.wc);
+    rc = f32_plain ? KV_OK : fill_mlp_const(a->mlp, (cudaStream_t)a->stream, &p.wc);
     if (rc != KV_OK) return rc;
     p.bins = bins;
     p.inv_bins = 1.0f / (float)bins;
@@ -1107,7 +1201,16 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
     cudaError_t e = cudaMemsetAsync(p.fb_count, 0, sizeof(uint32_t), s);
     const bool second = a->d2v || a->dvx || a->d2x;
     const bool deriv = a->dv || a->dx || second;
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && f32_plain) {
+        int64_t need = (a->n + kMlpBlock - 1) / kMlpBlock;
+        int64_t cap = (int64_t)sm_count() * 16;
+        int grid = (int)(need < cap ? need : cap);
+        if (second) kv_plain_f32_kernel<true, true><<<grid, kMlpBlock, 0, s>>>(p, max_iter);
+        else if (deriv) kv_plain_f32_kernel<true><<<grid, kMlpBlock, 0, s>>>(p, max_iter);
+        else kv_plain_f32_kernel<false><<<grid, kMlpBlock, 0, s>>>(p, max_iter);
+        note_launch();
+        e = cudaGetLastError();
+    } else if (e == cudaSuccess) {
         // persistent grid; at most 8 CTAs per SM so that their 64 TMEM columns each fit in 512
         const int per_sm = second  ? tc_blocks_per_sm(kv_mlp_tc_kernel<true, true>)
                            : deriv ? tc_blocks_per_sm(kv_mlp_tc_kernel<true>)
@@ -1126,6 +1229,7 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
         f.p = p;
         f.log_eps = log_eps;
         f.max_iter = max_iter;
+        f.try_f32 = f32_plain ? 0 : 1;
         f.fallback_total = a->fallback_count;
         int grid = sm_count() * 4;
         if (second) kv_fallback_kernel<true, true><<<grid, kMlpBlock, 0, s>>>(f);

@@ -111,7 +111,7 @@ def kv_fwd_bwd_ex(v, x, *, bins: int = 0, bracket: str = "plain", log_eps: float
     a.n = v.numel()
     a.bins = bins
     a.dtype = dt
-    a.bracket = {"plain": N.KV_BRACKET_PLAIN, "mlp": N.KV_BRACKET_MLP}[bracket]
+    a.bracket = {"plain": N.KV_BRACKET_PLAIN, "mlp": N.KV_BRACKET_MLP, "f32": N.KV_BRACKET_PLAIN_F32}[bracket]
     a.log_eps = log_eps
     a.max_iter = max_iter
     a.lanes = lanes
@@ -149,7 +149,7 @@ def kv_fwd_bwd_host(v, x, *, bins: int = 0, bracket: str = "plain", mlp=None, lo
     a.n = v.size
     a.bins = bins
     a.dtype = dt
-    a.bracket = {"plain": N.KV_BRACKET_PLAIN, "mlp": N.KV_BRACKET_MLP}[bracket]
+    a.bracket = {"plain": N.KV_BRACKET_PLAIN, "mlp": N.KV_BRACKET_MLP, "f32": N.KV_BRACKET_PLAIN_F32}[bracket]
     a.log_eps = log_eps
     a.mlp = mlp.handle if mlp is not None else None
     a.stream = _stream_ptr(torch.device("cuda", torch.cuda.current_device()))

@@ -103,3 +103,13 @@ def test_second_derivative_argument_errors(lib):
     assert lib.kv_grad2(None, fake, fake, fake, fake, fake, fake, fake, fake, None, None, 5, 0, None) == -1
     assert lib.kv_grad2(fake, fake, fake, fake, fake, fake, fake, fake, fake, None, None, 5, 9, None) == -4
     assert lib.kv_grad2(fake, fake, fake, fake, fake, fake, fake, fake, fake, None, None, -1, 0, None) == -2
+
+
+def test_f32_bracket_argument_errors(lib):
+    a = N.KvArgs()
+    a.v = a.x = a.logk = 256
+    a.n, a.bins, a.dtype = 10, 32, 0
+    a.bracket = N.KV_BRACKET_PLAIN_F32
+    assert lib.kv_fwd_bwd_ex(ctypes.byref(a)) == -4  # FP64 I/O has no FP32 bracket
+    a.bracket = 3
+    assert lib.kv_fwd_bwd_ex(ctypes.byref(a)) == -7
