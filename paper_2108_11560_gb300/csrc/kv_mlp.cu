@@ -664,11 +664,20 @@ __global__ void __launch_bounds__(kMlpBlock, 8) kv_mlp_tc_kernel(MlpPathParams p
     uint32_t phase = 0;
     bool aborted = false;
     int64_t base = (int64_t)blockIdx.x * kMlpBlock;
-    for (; base < p.n; base += (int64_t)gridDim.x * kMlpBlock) {
+    const int64_t stride = (int64_t)gridDim.x * kMlpBlock;
+    // this thread's inputs of the next tile are loaded one tile ahead, so their DRAM latency
+    // overlaps the current tile's work
+    float v_next = base + t < p.n ? __ldcs(p.v + base + t) : 1.0f;
+    float x_next = base + t < p.n ? __ldcs(p.x + base + t) : 1.0f;
+    for (; base < p.n; base += stride) {
         const int64_t i = base + t;
         const bool active = i < p.n;
-        const float v = active ? p.v[i] : 1.0f;
-        const float x = active ? p.x[i] : 1.0f;
+        const float v = v_next;
+        const float x = x_next;
+        if (i + stride < p.n) {
+            v_next = __ldcs(p.v + i + stride);
+            x_next = __ldcs(p.x + i + stride);
+        }
         float lk, dv, dx;
         const bool edge = float_edge(v, x, lk, dv, dx);
         const float va = edge ? 1.0f : fabsf(v);
