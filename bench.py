@@ -46,16 +46,16 @@ MIXED_LOG_EPS = -20.0
 #            need it, ~2.6), three block-compensated sums 5.25              -> 44 (+ 6 MUFU)
 #   per pair: layer 1 and layer 3 on the CUDA cores 256 (layer 2 runs on the tensor cores and
 #             is not counted), peak Newton, offset constants, endpoint check, setup and finish
-#             ~260                                                            -> 514
+#             ~256                                                            -> 512
 # ncu's executed FFMA + FADD + FMUL (+ 2 x FFMA2/FADD2/FMUL2) counters over 4M pairs at 1 and 32
-# bins give 44.16 per bin and 513.5 per pair (profiles/kv_mlp_tc_kernel_hard_band_4M.md).
+# bins give 44.16 per bin and 511.6 per pair (profiles/kv_mlp_tc_kernel_hard_band_4M.md).
 FP32_OPS_PER_BIN = 44.16
 MUFU_OPS_PER_BIN = 6
-FP32_OPS_PER_PAIR = 513.5
-# DRAM bytes per pair of the fast-path kernel, from one ncu capture (50.39 MB read + 8.68 MB
+FP32_OPS_PER_PAIR = 511.6
+# DRAM bytes per pair of the fast-path kernel, from one ncu capture (50.39 MB read + 5.25 MB
 # written for 4,194,304 pairs; profiles/kv_mlp_tc_kernel_hard_band_4M.md), scaled to a launch.
 # Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES_PER_PAIR = (50.387456e6 + 8.675584e6) / 4194304
+TRAFFIC_BYTES_PER_PAIR = (50.388224e6 + 5.249536e6) / 4194304
 
 
 def _peaks():
