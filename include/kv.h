@@ -147,9 +147,10 @@ int kv_fwd_bwd_ex(const kv_args* a);
  * (pinned with cudaHostAlloc for full speed); every other field means what it means for
  * kv_fwd_bwd_ex, except that grad_out, status, fallback_count and the second-derivative outputs
  * must be NULL (else KV_ERR_ARG).  The call copies the inputs to the device, computes and copies
- * the outputs back, pipelined in chunks of up to 2^19 pairs rotating over a->stream and three
- * internal streams, and returns when the host outputs are complete.  Device staging memory is
- * allocated and freed on the stream inside the call. */
+ * the outputs back, pipelined in chunks of up to 2^19 pairs over four buffer slots (internal
+ * streams for the copies in, the copies out and each slot's kernels, ordered by events and
+ * started after the work already on a->stream), and returns when the host outputs are complete.
+ * Device staging memory is allocated and freed on a->stream inside the call. */
 int kv_fwd_bwd_host(const kv_args* a);
 
 /* ------------------------------------------------------------------ building blocks */

@@ -715,19 +715,35 @@ int kv_fwd_bwd_host(const kv_args* h)
     const int64_t nchunks = (n + chunk - 1) / chunk;
     const int nslots = nchunks < KV_HOST_SLOTS ? (int)nchunks : KV_HOST_SLOTS;
     const bool mlp = h->bracket != KV_BRACKET_PLAIN;  // the paths with a fallback list
-    const size_t slot_bytes = 5 * es * chunk + (mlp ? sizeof(uint32_t) * (chunk + 32) : 0);
-    cudaStream_t st[KV_HOST_SLOTS] = {(cudaStream_t)h->stream};
-    cudaError_t e = cudaSuccess;
-    for (int k = 1; k < nslots && e == cudaSuccess; ++k)
-        e = cudaStreamCreateWithFlags(&st[k], cudaStreamNonBlocking);
-    char* buf = nullptr;
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&buf, slot_bytes * nslots, st[0]);
-    cudaEvent_t ev = nullptr;
-    if (e == cudaSuccess && nslots > 1) {
-        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventRecord(ev, st[0]);
-        for (int k = 1; k < nslots && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(st[k], ev, 0);
+    // a slot: inputs (2 arrays) and outputs (3 arrays) with separate lifetimes, and the fallback
+    // list of the learned path
+    const size_t in_bytes = 2 * es * chunk, out_bytes = 3 * es * chunk;
+    const size_t slot_bytes = in_bytes + out_bytes + (mlp ? sizeof(uint32_t) * (chunk + 32) : 0);
+    // streams: one for host-to-device copies, one for device-to-host copies, one per slot for
+    // the kernels; events order them.  An input slot is refilled as soon as its kernel has read
+    // it, an output slot as soon as its copy-out is done, so the copy engines never wait for a
+    // whole slot cycle.
+    cudaStream_t caller = (cudaStream_t)h->stream;
+    cudaStream_t sin = nullptr, sout = nullptr, sk[KV_HOST_SLOTS] = {};
+    cudaEvent_t start = nullptr, in_ready[KV_HOST_SLOTS] = {}, done[KV_HOST_SLOTS] = {},
+                out_free[KV_HOST_SLOTS] = {};
+    bool used_in[KV_HOST_SLOTS] = {}, used_out[KV_HOST_SLOTS] = {};
+    cudaError_t e = cudaStreamCreateWithFlags(&sin, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sout, cudaStreamNonBlocking);
+    for (int k = 0; k < nslots && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&sk[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+    for (int k = 0; k < nslots && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&in_ready[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&out_free[k], cudaEventDisableTiming);
     }
+    char* buf = nullptr;
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&buf, slot_bytes * nslots, caller);
+    // everything starts after the caller's stream has reached this call (and the allocation)
+    if (e == cudaSuccess) e = cudaEventRecord(start, caller);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sin, start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, start, 0);
+    for (int k = 0; k < nslots && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(sk[k], start, 0);
     for (int64_t c = 0; e == cudaSuccess && rc == KV_OK && c < nchunks; ++c) {
         const int k = (int)(c % nslots);
         const int64_t off = c * chunk;
@@ -735,14 +751,21 @@ int kv_fwd_bwd_host(const kv_args* h)
         char* base = buf + slot_bytes * k;
         char* dvin = base;
         char* dxin = base + es * chunk;
-        char* dl = base + 2 * es * chunk;
-        char* ddv = base + 3 * es * chunk;
-        char* ddx = base + 4 * es * chunk;
-        uint32_t* scratch = mlp ? (uint32_t*)(base + 5 * es * chunk) : nullptr;
-        e = cudaMemcpyAsync(dvin, (const char*)h->v + es * off, es * m, cudaMemcpyHostToDevice, st[k]);
+        char* dl = base + in_bytes;
+        char* ddv = dl + es * chunk;
+        char* ddx = ddv + es * chunk;
+        uint32_t* scratch = mlp ? (uint32_t*)(base + in_bytes + out_bytes) : nullptr;
+        // copy in once the slot's previous kernel has read its inputs
+        if (used_in[k]) e = cudaStreamWaitEvent(sin, done[k], 0);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(dxin, (const char*)h->x + es * off, es * m, cudaMemcpyHostToDevice,
-                                st[k]);
+            e = cudaMemcpyAsync(dvin, (const char*)h->v + es * off, es * m, cudaMemcpyHostToDevice, sin);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dxin, (const char*)h->x + es * off, es * m, cudaMemcpyHostToDevice, sin);
+        if (e == cudaSuccess) e = cudaEventRecord(in_ready[k], sin);
+        used_in[k] = true;
+        // compute once the inputs are in and the slot's previous outputs have been copied out
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sk[k], in_ready[k], 0);
+        if (e == cudaSuccess && used_out[k]) e = cudaStreamWaitEvent(sk[k], out_free[k], 0);
         if (e != cudaSuccess) break;
         kv_args d = *h;
         d.v = dvin;
@@ -751,31 +774,45 @@ int kv_fwd_bwd_host(const kv_args* h)
         d.dv = h->dv ? ddv : nullptr;
         d.dx = h->dx ? ddx : nullptr;
         d.n = m;
-        d.stream = st[k];
+        d.stream = sk[k];
         rc = kvh::fwd_bwd_ex(&d, scratch);
         if (rc != KV_OK) break;
-        if (h->logk)
-            e = cudaMemcpyAsync((char*)h->logk + es * off, dl, es * m, cudaMemcpyDeviceToHost, st[k]);
+        e = cudaEventRecord(done[k], sk[k]);
+        // copy out once the kernel is done
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, done[k], 0);
+        if (e == cudaSuccess && h->logk)
+            e = cudaMemcpyAsync((char*)h->logk + es * off, dl, es * m, cudaMemcpyDeviceToHost, sout);
         if (e == cudaSuccess && h->dv)
-            e = cudaMemcpyAsync((char*)h->dv + es * off, ddv, es * m, cudaMemcpyDeviceToHost, st[k]);
+            e = cudaMemcpyAsync((char*)h->dv + es * off, ddv, es * m, cudaMemcpyDeviceToHost, sout);
         if (e == cudaSuccess && h->dx)
-            e = cudaMemcpyAsync((char*)h->dx + es * off, ddx, es * m, cudaMemcpyDeviceToHost, st[k]);
+            e = cudaMemcpyAsync((char*)h->dx + es * off, ddx, es * m, cudaMemcpyDeviceToHost, sout);
+        if (e == cudaSuccess) e = cudaEventRecord(out_free[k], sout);
+        used_out[k] = true;
     }
-    // join the internal streams back into the caller's before the buffer goes
-    for (int k = 1; k < nslots && ev; ++k) {
-        cudaError_t e2 = cudaEventRecord(ev, st[k]);
-        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(st[0], ev, 0);
+    // join every internal stream into the caller's before the buffer goes
+    cudaStream_t all[KV_HOST_SLOTS + 2] = {sin, sout};
+    for (int k = 0; k < nslots; ++k) all[2 + k] = sk[k];
+    for (int k = 0; k < nslots + 2; ++k) {
+        if (!all[k] || !start) continue;
+        cudaError_t e2 = cudaEventRecord(start, all[k]);
+        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(caller, start, 0);
         if (e == cudaSuccess) e = e2;
     }
     if (buf) {
-        cudaError_t e2 = cudaFreeAsync(buf, st[0]);
+        cudaError_t e2 = cudaFreeAsync(buf, caller);
         if (e == cudaSuccess) e = e2;
     }
-    cudaError_t e3 = cudaStreamSynchronize(st[0]);
+    cudaError_t e3 = cudaStreamSynchronize(caller);
     if (e == cudaSuccess) e = e3;
-    if (ev) cudaEventDestroy(ev);
-    for (int k = 1; k < nslots; ++k)
-        if (st[k]) cudaStreamDestroy(st[k]);
+    for (int k = 0; k < nslots; ++k) {
+        if (in_ready[k]) cudaEventDestroy(in_ready[k]);
+        if (done[k]) cudaEventDestroy(done[k]);
+        if (out_free[k]) cudaEventDestroy(out_free[k]);
+        if (sk[k]) cudaStreamDestroy(sk[k]);
+    }
+    if (start) cudaEventDestroy(start);
+    if (sin) cudaStreamDestroy(sin);
+    if (sout) cudaStreamDestroy(sout);
     if (rc != KV_OK) return rc;
     if (e != cudaSuccess) return kvh::cuda_fail(e);
     return KV_OK;

@@ -1240,7 +1240,7 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
         f.max_iter = max_iter;
         f.try_f32 = f32_plain ? 0 : 1;
         f.fallback_total = a->fallback_count;
-        int grid = sm_count() * 4;
+        int grid = sm_count();  // grid-stride over the list; most calls have none
         if (second) kv_fallback_kernel<true, true><<<grid, kMlpBlock, 0, s>>>(f);
         else if (deriv) kv_fallback_kernel<true><<<grid, kMlpBlock, 0, s>>>(f);
         else kv_fallback_kernel<false><<<grid, kMlpBlock, 0, s>>>(f);
