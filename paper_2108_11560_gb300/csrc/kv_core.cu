@@ -16,10 +16,13 @@
 
 #include <atomic>
 
-// The host-buffer entry point streams 2^KV_HOST_CHUNK_LOG2 pairs per chunk through
-// KV_HOST_SLOTS device buffer slots, one stream each (copy in, compute, copy out).
+// The host-buffer entry point streams chunks of 2^KV_HOST_MIN_CHUNK_LOG2 up to
+// 2^KV_HOST_CHUNK_LOG2 pairs through KV_HOST_SLOTS device buffer slots.
 #ifndef KV_HOST_CHUNK_LOG2
 #define KV_HOST_CHUNK_LOG2 19
+#endif
+#ifndef KV_HOST_MIN_CHUNK_LOG2
+#define KV_HOST_MIN_CHUNK_LOG2 19
 #endif
 #ifndef KV_HOST_SLOTS
 #define KV_HOST_SLOTS 4
@@ -711,8 +714,19 @@ int kv_fwd_bwd_host(const kv_args* h)
     const int64_t n = h->n;
     if (n == 0) return KV_OK;
     const size_t es = kvh::elem_size(h->dtype);
-    const int64_t chunk = n < ((int64_t)1 << KV_HOST_CHUNK_LOG2) ? n : ((int64_t)1 << KV_HOST_CHUNK_LOG2);
-    const int64_t nchunks = (n + chunk - 1) / chunk;
+    // chunk sizes: doubling from the minimum at the start and halving towards the end (short
+    // fill and drain of the pipeline), the maximum in between (few launches)
+    const int64_t cmax = (int64_t)1 << KV_HOST_CHUNK_LOG2, cmin = (int64_t)1 << KV_HOST_MIN_CHUNK_LOG2;
+    const int64_t chunk = n < cmax ? n : cmax;  // the slot size
+    auto chunk_size = [&](int64_t c, int64_t left) {
+        int64_t sz = cmin << (c < 20 ? c : 20);
+        if (sz > left / 2) sz = left / 2;
+        if (sz < cmin) sz = cmin;
+        if (sz > chunk) sz = chunk;
+        return sz < left ? sz : left;
+    };
+    int64_t nchunks = 0;
+    for (int64_t off = 0; off < n; ++nchunks) off += chunk_size(nchunks, n - off);
     const int nslots = nchunks < KV_HOST_SLOTS ? (int)nchunks : KV_HOST_SLOTS;
     const bool mlp = h->bracket != KV_BRACKET_PLAIN;  // the paths with a fallback list
     // a slot: inputs (2 arrays) and outputs (3 arrays) with separate lifetimes, and the fallback
@@ -744,10 +758,10 @@ int kv_fwd_bwd_host(const kv_args* h)
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sin, start, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, start, 0);
     for (int k = 0; k < nslots && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(sk[k], start, 0);
+    int64_t off = 0;
     for (int64_t c = 0; e == cudaSuccess && rc == KV_OK && c < nchunks; ++c) {
         const int k = (int)(c % nslots);
-        const int64_t off = c * chunk;
-        const int64_t m = (n - off) < chunk ? (n - off) : chunk;
+        const int64_t m = chunk_size(c, n - off);
         char* base = buf + slot_bytes * k;
         char* dvin = base;
         char* dxin = base + es * chunk;
@@ -788,6 +802,7 @@ int kv_fwd_bwd_host(const kv_args* h)
             e = cudaMemcpyAsync((char*)h->dx + es * off, ddx, es * m, cudaMemcpyDeviceToHost, sout);
         if (e == cudaSuccess) e = cudaEventRecord(out_free[k], sout);
         used_out[k] = true;
+        off += m;
     }
     // join every internal stream into the caller's before the buffer goes
     cudaStream_t all[KV_HOST_SLOTS + 2] = {sin, sout};
