@@ -699,10 +699,10 @@ int kv_sum(const void* a, int64_t n, int dtype, double* out, void* stream)
     return KV_OK;
 }
 
-// Host-buffer form: chunks of up to 2^20 pairs rotate over three streams (the caller's and two
-// internal ones); each stream copies its chunk in, computes it and copies it out in order, so
-// one chunk's input copy, another's kernels and a third's output copy run at the same time.
-// Device buffers (and the learned path's fallback lists) are allocated once per call.
+// Host-buffer form: chunks rotate over KV_HOST_SLOTS device buffer slots; one internal stream
+// copies inputs in, one copies outputs out and one per slot runs the kernels, ordered by events,
+// so one chunk's input copy, other chunks' kernels and another's output copy run at the same
+// time.  Device buffers (and the learned path's fallback lists) are allocated once per call.
 int kv_fwd_bwd_host(const kv_args* h)
 {
     if (!h) return KV_ERR_NULL;
