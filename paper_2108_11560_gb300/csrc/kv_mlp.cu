@@ -8,7 +8,7 @@
 //   L_k = y_k * out[2k] + out[2k+1];  t0 = max(t_ref - max(e^{L_0} - DELTA, 0), 0),
 //   t1 = t_ref + max(e^{L_1} - DELTA, 0), with t_ref the peak of g.
 // The network predicts log half-widths of the range about the peak; the peak itself comes from
-// three FP32 Newton steps on g' from asinh(v/x) (g' is concave and <= 0 there, so the iterates
+// two FP32 Newton steps on g' from asinh(v/x) (g' is concave and <= 0 there, so the iterates
 // fall monotonically onto the zero).
 //
 // Fast path per pair (kv_mlp_tc_kernel): MLP (hidden layer on the tensor cores) -> peak ->
@@ -155,12 +155,13 @@ __device__ __forceinline__ float fast_asinh(float z)
 }
 
 // The peak of g by STEPS FP32 Newton steps from asinh(v/x) (0 when v^2 <= x).  On the fast path
-// (three steps) its accuracy does not enter the results (the bins are exact relative to any
+// (two steps: a third changed neither the fallback rate nor the results) its accuracy does not
+// enter the results (the bins are exact relative to any
 // reference point near the peak); the training targets and the raw predictions, which are
 // measured from the peak, take eight.  The steps use the approximate exponential, reciprocal and
 // division.  The start is nudged up so that it stays on the side of the zero where g' <= 0
 // despite the approximate asinh.
-template <int STEPS = 3>
+template <int STEPS = 2>
 __device__ __forceinline__ float peak_f32(float v, float x)
 {
     if (!(v * v > x)) return 0.0f;
