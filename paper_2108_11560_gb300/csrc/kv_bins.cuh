@@ -72,9 +72,14 @@ __device__ __forceinline__ T lane_sum(T a)
 struct BinsD {
     double v, x, t0, h, tp, s0, Lu;  // s0 = t0 - t_p, Lu = log1p(e^{-2 v t_p})
     double e2u;                      // e^{-2 v t_p} (second derivatives only)
+    double ep, em;                   // e^{t_p}, e^{-t_p}
     int n;
 };
 
+// FP64 bins.  Per bin five transcendentals: e^{-2vt}, log1p of it, sinh((t + t_p)/2),
+// expm1(s/2) and the weight's exp.  x (cosh t - cosh t_p) = 2 x sinh((t + t_p)/2) sinh(s/2) with
+// sinh(s/2) = (E - 1)(1 + 1/E)/2 from E - 1 = expm1(s/2) (no cancellation at small s), and
+// cosh t = (e^{t_p} E^2 + e^{-t_p} E^-2)/2, a sum of positive terms.
 template <int L, bool DERIV>
 __device__ __forceinline__ void sums_f64(const BinsD& b, int lane, double& S0, double& S1, double& S2)
 {
@@ -86,14 +91,18 @@ __device__ __forceinline__ void sums_f64(const BinsD& b, int lane, double& S0, d
         double t = b.t0 + m * b.h;
         double s = b.s0 + m * b.h;
         double e2 = exp(-2.0 * b.v * t);
-        double dlc = b.v * s + (log1p(e2) - b.Lu);                   // log cosh(vt) - log cosh(u)
-        double dxc = 2.0 * b.x * sinh(0.5 * (t + b.tp)) * sinh(0.5 * s); // x (cosh t - cosh t_p)
+        double dlc = b.v * s + (log1p(e2) - b.Lu);  // log cosh(vt) - log cosh(u)
+        const double em1 = expm1(0.5 * s);
+        const double ri = 1.0 / (1.0 + em1);                           // e^{-s/2}
+        const double sh = 0.5 * em1 * (1.0 + ri);                      // sinh(s/2)
+        double dxc = 2.0 * b.x * sinh(0.5 * (t + b.tp)) * sh;          // x (cosh t - cosh t_p)
         double c = (m == 0 || m == b.n) ? 0.5 : 1.0;
         double w = c * exp(dlc - dxc);
         k0.add(w);
         if (DERIV) {
             k1.add(w * t * ((1.0 - e2) / (1.0 + e2)));
-            k2.add(w * cosh(t));
+            const double eh = 1.0 + em1;                               // e^{s/2}
+            k2.add(w * (0.5 * fma(b.ep, eh * eh, b.em * (ri * ri)))); // cosh t
         }
     }
     S0 = lane_sum<double, L>(k0.value());

@@ -174,6 +174,8 @@ __global__ void __launch_bounds__(kBlock) kv_f64_kernel(KParams p)
         b.tp = br.tp;
         b.s0 = br.t0 - br.tp;
         b.Lu = log1p(exp(-2.0 * va * br.tp));
+        b.ep = exp(br.tp);
+        b.em = 1.0 / b.ep;
         b.n = p.bins;
         if constexpr (D2) {
             b.e2u = exp(-2.0 * va * br.tp);
