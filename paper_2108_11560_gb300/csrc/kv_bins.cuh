@@ -120,6 +120,7 @@ struct BinsF {
     float lu;       // log1p(e^{-2u})
     float ep, em;   // e^{t_p}, e^{-t_p}
     float e2u, shp; // e^{-2u}, sinh t_p (second derivatives only)
+    float xch, xsh; // x cosh t_p, x sinh t_p
     int n;
 };
 
@@ -218,6 +219,7 @@ __device__ __forceinline__ float delta_g_slope_f32(const BinsF& b, float e2, flo
 struct BinsK {
     float c1, ap, am, lu;  // v - x sinh t_p, x e^{+-t_p}/2, log1p(e^{-2u}), each times log2 e
     float hep, hem;        // e^{+-t_p} / 2
+    float cA, cB, lA;      // x cosh t_p, x sinh t_p and log1p(e^{-2u}) - x cosh t_p, times log2 e
 };
 
 __device__ __forceinline__ BinsK bins_k(const BinsF& b)
@@ -229,7 +231,41 @@ __device__ __forceinline__ BinsK bins_k(const BinsF& b)
     k.lu = b.lu * LOG2E_F;
     k.hep = 0.5f * b.ep;
     k.hem = 0.5f * b.em;
+    k.cA = b.xch * LOG2E_F;
+    k.cB = b.xsh * LOG2E_F;
+    k.lA = (b.lu - b.xch) * LOG2E_F;
     return k;
+}
+
+// The x-part of the exponent plus the log1p offset, X = (x e^{t_p}/2) phi(s) + (x e^{-t_p}/2) phi(-s)
+// + log1p(e^{-2u}) (times log2 e), for two bins:
+//   |s| <= 1: phi(+-s) = z (E(z) +- s O(z)), so X = z (x cosh t_p E + x sinh t_p s O) + lu;
+//   |s| > 1:  X = (x e^{t_p}/2) e^s + (x e^{-t_p}/2) e^{-s} - x sinh t_p s + lu - x cosh t_p;
+// e^{+-s} (es, ems) are returned for the cosh t integrand.
+__device__ __forceinline__ float2 x_part2(const BinsK& k, float2 s, float2& es, float2& ems)
+{
+    const float2 z = mul2(s, s);
+    float2 E, O;
+    KV_PHI_SERIES(mul2, fma2, f2, z, E, O)
+    const float2 so = mul2(s, O);
+    const float2 xs = fma2(z, fma2(f2(k.cA), E, mul2(f2(k.cB), so)), f2(k.lu));
+    const float2 el = mul2(s, f2(LOG2E_F));
+    es = make_float2(ex2_approx(el.x), ex2_approx(el.y));
+    ems = make_float2(rcp_approx(es.x), rcp_approx(es.y));
+    const float2 xl = fma2(f2(k.ap), es, fma2(f2(k.am), ems, fma2(f2(-k.cB), s, f2(k.lA))));
+    return make_float2(fabsf(s.x) <= PHI_SERIES_MAX ? xs.x : xl.x, fabsf(s.y) <= PHI_SERIES_MAX ? xs.y : xl.y);
+}
+
+__device__ __forceinline__ float x_part(const BinsK& k, float s, float& es, float& ems)
+{
+    const float z = s * s;
+    float E, O;
+    KV_PHI_SERIES(__fmul_rn, fmaf, f1, z, E, O)
+    const float xs = fmaf(z, fmaf(k.cA, E, k.cB * (s * O)), k.lu);
+    es = ex2_approx(s * LOG2E_F);
+    ems = rcp_approx(es);
+    const float xl = fmaf(k.ap, es, fmaf(k.am, ems, fmaf(-k.cB, s, k.lA)));
+    return fabsf(s) <= PHI_SERIES_MAX ? xs : xl;
 }
 
 // vt below this uses tanh_small
@@ -243,12 +279,12 @@ __device__ __forceinline__ void bin_f32(const BinsF& b, const BinsK& k, float mf
                                         float& w1, float& w2)
 {
     const float s = fmaf(mf, b.h, b.s0);
-    float php, phm, es, ems;
-    phi_pair(s, php, phm, es, ems);
+    float es, ems;
+    const float X = x_part(k, s, es, ems);
     const float vt = fmaf(b.v, s, b.u);
     const float e2 = ex2_approx(-2.0f * LOG2E_F * vt);  // e^{-2vt}
     // (g(t) - g(t_p)) log2 e with log1p(e^{-2vt}) - log1p(e^{-2u}) as lg2(1 + e2) - lu
-    const float dg = fmaf(k.c1, s, lg2_approx(1.0f + e2)) - fmaf(k.ap, php, fmaf(k.am, phm, k.lu));
+    const float dg = fmaf(k.c1, s, lg2_approx(1.0f + e2)) - X;
     w = c * ex2_approx(dg);
     if (DERIV) {
         const float t = b.tp + s;
@@ -262,23 +298,6 @@ __device__ __forceinline__ void bin_f32(const BinsF& b, const BinsK& k, float mf
 }
 
 // ------------------------------------------------------------------ two bins per instruction
-
-// phi_pair for two values of s.
-__device__ __forceinline__ void phi_pair2(float2 s, float2& php, float2& phm, float2& es, float2& ems)
-{
-    const float2 z = mul2(s, s);
-    float2 E, O;
-    KV_PHI_SERIES(mul2, fma2, f2, z, E, O)
-    const float2 so = mul2(s, O);
-    const float2 pp = mul2(z, add2(E, so)), pm = mul2(z, sub2(E, so));
-    const float2 el = mul2(s, f2(LOG2E_F));
-    es = make_float2(ex2_approx(el.x), ex2_approx(el.y));
-    ems = make_float2(rcp_approx(es.x), rcp_approx(es.y));
-    const float2 bp = sub2(add2(es, f2(-1.0f)), s), bm = add2(add2(ems, f2(-1.0f)), s);
-    const bool kx = fabsf(s.x) <= PHI_SERIES_MAX, ky = fabsf(s.y) <= PHI_SERIES_MAX;
-    php = make_float2(kx ? pp.x : bp.x, ky ? pp.y : bp.y);
-    phm = make_float2(kx ? pm.x : bm.x, ky ? pm.y : bm.y);
-}
 
 __device__ __forceinline__ float2 tanh_small2(float2 y)
 {
@@ -298,14 +317,14 @@ __device__ __forceinline__ void bin_f32x2(const BinsF& b, const BinsK& k, float2
                                           float2& w1, float2& w2)
 {
     const float2 s = fma2(mf, f2(b.h), f2(b.s0));
-    float2 php, phm, es, ems;
-    phi_pair2(s, php, phm, es, ems);
+    float2 es, ems;
+    const float2 X = x_part2(k, s, es, ems);
     const float2 vt = fma2(f2(b.v), s, f2(b.u));
     const float2 ea = mul2(vt, f2(-2.0f * LOG2E_F));
     const float2 e2 = make_float2(ex2_approx(ea.x), ex2_approx(ea.y));  // e^{-2vt}
     const float2 ope = add2(f2(1.0f), e2);
     const float2 lg = make_float2(lg2_approx(ope.x), lg2_approx(ope.y));
-    const float2 dg = sub2(fma2(f2(k.c1), s, lg), fma2(f2(k.ap), php, fma2(f2(k.am), phm, f2(k.lu))));
+    const float2 dg = sub2(fma2(f2(k.c1), s, lg), X);
     w = make_float2(c0 * ex2_approx(dg.x), ex2_approx(dg.y));
     if (DERIV) {
         const float2 t = add2(f2(b.tp), s);

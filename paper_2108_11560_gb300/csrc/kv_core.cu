@@ -252,6 +252,8 @@ __global__ void __launch_bounds__(kBlock) kv_mixed_kernel(KParams p)
         b.lu = (float)log1p(exp(-2.0 * u));
         b.ep = (float)ep;
         b.em = (float)em;
+        b.xch = (float)(xa * cosh(br.tp));
+        b.xsh = (float)(xa * sinh(br.tp));
         b.n = p.bins;
         if constexpr (D2) {
             const double e2u = exp(-2.0 * u);

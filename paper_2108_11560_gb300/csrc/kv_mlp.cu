@@ -328,6 +328,8 @@ __device__ __forceinline__ PeakConst peak_constants(float v, float x, float tp, 
     c.b.e2u = e2u;
     const df shr = df_sub_fast(E, Ei);  // 2 sinh t_r
     c.b.shp = 0.5f * (shr.hi + shr.lo);
+    c.b.xch = ch.hi + ch.lo;
+    c.b.xsh = sh.hi + sh.lo;
     return c;
 }
 
@@ -882,6 +884,8 @@ __global__ void __launch_bounds__(kMlpBlock) kv_fallback_kernel(FallbackParams f
         b.lu = (float)log1p(exp(-2.0 * u));
         b.ep = (float)ep;
         b.em = (float)em;
+        b.xch = (float)(x * cosh(br.tp));
+        b.xsh = (float)(x * sinh(br.tp));
         b.n = p.bins;
         float S0, S1, S2;
         if constexpr (D2) {
