@@ -41,21 +41,22 @@ MIXED_LOG_EPS = -20.0
 
 # Algorithmic FP32 work of the learned-bracket fast path, counted operation by operation from
 # its formulas with an FMA as one operation and a paired (f32x2) instruction as two:
-#   per bin: the abscissa 1, phi(+-s) and e^{+-s} 20, the exponent g - g(t_p) and its inputs 7,
-#            the two derivative integrands 8 (+ the tanh series in the ~37 % of warp-blocks that
-#            need it, ~2.6), three block-compensated sums 5.25              -> 44 (+ 6 MUFU)
+#   per bin: the abscissa 1, the exponent's x-part (the phi series or e^{+-s}) and log1p offset
+#            18, the rest of the exponent 5, the two derivative integrands 8 (+ the tanh series in
+#            the ~37 % of warp-blocks that need it, ~2.6), three block-compensated sums 5.25
+#                                                                               -> 40 (+ 6 MUFU)
 #   per pair: layer 1 and layer 3 on the CUDA cores 256 (layer 2 runs on the tensor cores and
 #             is not counted), peak Newton, offset constants, endpoint check, setup and finish
-#             ~256                                                            -> 512
+#             ~250                                                              -> 507
 # ncu's executed FFMA + FADD + FMUL (+ 2 x FFMA2/FADD2/FMUL2) counters over 4M pairs at 1 and 32
-# bins give 44.16 per bin and 511.6 per pair (profiles/kv_mlp_tc_kernel_hard_band_4M.md).
-FP32_OPS_PER_BIN = 44.16
+# bins give 40.11 per bin and 506.7 per pair (profiles/kv_mlp_tc_kernel_hard_band_4M.md).
+FP32_OPS_PER_BIN = 40.11
 MUFU_OPS_PER_BIN = 6
-FP32_OPS_PER_PAIR = 511.6
-# DRAM bytes per pair of the fast-path kernel, from one ncu capture (50.39 MB read + 5.25 MB
+FP32_OPS_PER_PAIR = 506.7
+# DRAM bytes per pair of the fast-path kernel, from one ncu capture (50.40 MB read + 4.92 MB
 # written for 4,194,304 pairs; profiles/kv_mlp_tc_kernel_hard_band_4M.md), scaled to a launch.
 # Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES_PER_PAIR = (50.388224e6 + 5.249536e6) / 4194304
+TRAFFIC_BYTES_PER_PAIR = (50.396928e6 + 4.91648e6) / 4194304
 
 
 def _peaks():
