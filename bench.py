@@ -41,22 +41,22 @@ MIXED_LOG_EPS = -20.0
 
 # Algorithmic FP32 work of the learned-bracket fast path, counted operation by operation from
 # its formulas with an FMA as one operation and a paired (f32x2) instruction as two:
-#   per bin: the abscissa 1, the exponent's x-part (the phi series or e^{+-s}) and log1p offset
-#            18, the rest of the exponent 5, the two derivative integrands 8 (+ the tanh series in
-#            the ~37 % of warp-blocks that need it, ~2.6), three block-compensated sums 5.25
-#                                                                               -> 40 (+ 6 MUFU)
+#   per bin: the abscissa 1, the exponent's x-part (the phi polynomials or e^{+-s}) 15, the rest
+#            of the weight 5, the two derivative integrands 7 (+ the tanh polynomial in the ~33 %
+#            of warp-blocks that need it, ~2.7), three block-compensated sums 5.25
+#                                                                               -> 36 (+ 4 MUFU)
 #   per pair: layer 1 and layer 3 on the CUDA cores 256 (layer 2 runs on the tensor cores and
 #             is not counted), peak Newton, offset constants, endpoint check, setup and finish
-#             ~250                                                              -> 507
+#             ~250                                                              -> 505
 # ncu's executed FFMA + FADD + FMUL (+ 2 x FFMA2/FADD2/FMUL2) counters over 4M pairs at 1 and 32
-# bins give 40.11 per bin and 506.7 per pair (profiles/kv_mlp_tc_kernel_hard_band_4M.md).
-FP32_OPS_PER_BIN = 40.11
-MUFU_OPS_PER_BIN = 6
-FP32_OPS_PER_PAIR = 506.7
-# DRAM bytes per pair of the fast-path kernel, from one ncu capture (50.40 MB read + 4.92 MB
+# bins give 35.92 per bin and 505.1 per pair (profiles/kv_mlp_tc_kernel_hard_band_4M.md).
+FP32_OPS_PER_BIN = 35.92
+MUFU_OPS_PER_BIN = 4
+FP32_OPS_PER_PAIR = 505.1
+# DRAM bytes per pair of the fast-path kernel, from one ncu capture (50.39 MB read + 5.11 MB
 # written for 4,194,304 pairs; profiles/kv_mlp_tc_kernel_hard_band_4M.md), scaled to a launch.
 # Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES_PER_PAIR = (50.396928e6 + 4.91648e6) / 4194304
+TRAFFIC_BYTES_PER_PAIR = (50.385664e6 + 5.10976e6) / 4194304
 
 
 def _peaks():
@@ -172,8 +172,10 @@ def run_reference(args):
 
 
 def end_to_end(args, vf, xf, mlp, dist, dev, world):
-    """The same call through the host-buffer entry point: pinned inputs copied in, outputs
-    copied out, inside the timed region (wall clock around the blocking call)."""
+    """The same call through the host-buffer entry point on pinned host buffers, inside the timed
+    region (wall clock around the blocking call): the inputs cross to the GPU and the results
+    come back every step, either staged through device buffers by copies or read and written
+    in place by the kernels over a coherent CPU-GPU link (transfer "auto" picks)."""
     import torch
 
     from paper_2108_11560_gb300 import kv
@@ -183,17 +185,22 @@ def end_to_end(args, vf, xf, mlp, dist, dev, world):
     hx = torch.from_numpy(xf).pin_memory().numpy()
     hout = tuple(torch.empty(n, dtype=torch.float32).pin_memory().numpy() for _ in range(3))
     steps = max(3, min(args.steps, 5))
-    kv.kv_fwd_bwd_host(hv, hx, bins=args.bins, bracket=args.bracket, mlp=mlp, out=hout)
+    kw = dict(bins=args.bins, bracket=args.bracket, mlp=mlp, out=hout, transfer=args.e2e_transfer)
+    kv.kv_fwd_bwd_host(hv, hx, **kw)
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(steps):
-        kv.kv_fwd_bwd_host(hv, hx, bins=args.bins, bracket=args.bracket, mlp=mlp, out=hout)
+        kv.kv_fwd_bwd_host(hv, hx, **kw)
     secs = time.perf_counter() - t0
     if dist:
         secs = all_reduce_scalar(secs, "max", device=dev)
+    mode = args.e2e_transfer
+    if mode == "auto":
+        mode = "direct" if kv.host_direct_supported() else "staged"
     return {"value": world * n * steps / secs, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * n,
-            "d2h_bytes_per_step": 3 * 4 * n}
+            "d2h_bytes_per_step": 3 * 4 * n, "transfer": mode,
+            "host_buffers": "pinned (torch pin_memory)"}
 
 
 def main():
@@ -206,6 +213,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--e2e-transfer", choices=("auto", "staged", "direct"), default="auto",
+                    help="how the host-buffer leg moves the data (kv_fwd_bwd_host_ex)")
     ap.add_argument("--pairs", type=int, default=N_PAIRS, help="pairs per GPU (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:

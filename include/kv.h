@@ -143,15 +143,41 @@ enum kv_pair_status {
  * optional fused gradient epilogue, per-pair status and fallback counter. */
 int kv_fwd_bwd_ex(const kv_args* a);
 
-/* kv_fwd_bwd_ex on HOST buffers: a->v, a->x, a->logk, a->dv and a->dx are host pointers
- * (pinned with cudaHostAlloc for full speed); every other field means what it means for
- * kv_fwd_bwd_ex, except that grad_out, status, fallback_count and the second-derivative outputs
- * must be NULL (else KV_ERR_ARG).  The call copies the inputs to the device, computes and copies
- * the outputs back, pipelined in chunks of up to 2^19 pairs over four buffer slots (internal
- * streams for the copies in, the copies out and each slot's kernels, ordered by events and
- * started after the work already on a->stream), and returns when the host outputs are complete.
- * Device staging memory is allocated and freed on a->stream inside the call. */
+/* How kv_fwd_bwd_host_ex moves the data between host and device. */
+enum kv_host_transfer {
+    /* DIRECT when every buffer is device-addressable host memory (see DIRECT) and the device
+     * reaches host memory over a coherent link (native host atomics or host page-table access,
+     * as on NVLink-C2C Grace systems: kv_host_direct_supported() == 1), else STAGED. */
+    KV_HOST_AUTO = 0,
+    /* Copies through device buffers: chunks of up to 2^19 pairs pipelined over four buffer
+     * slots (internal streams for the copies in, the copies out and each slot's kernels, ordered
+     * by events and started after the work already on a->stream).  Device staging memory is
+     * allocated and freed on a->stream inside the call.  Any host memory; pinned
+     * (cudaHostAlloc) for full copy speed. */
+    KV_HOST_STAGED = 1,
+    /* No staging copies: the kernels read v and x from, and write the outputs to, the host
+     * buffers themselves over the CPU-GPU link.  Every buffer must be page-locked host memory
+     * mapped into the device's address space over its whole length (cudaHostAlloc /
+     * cudaMallocHost under unified addressing, or cudaHostRegister with cudaHostRegisterMapped);
+     * the call checks both ends of each buffer and returns KV_ERR_ARG otherwise, without
+     * launching anything.  The fallback list of the learned path is device memory allocated on
+     * a->stream. */
+    KV_HOST_DIRECT = 2
+};
+
+/* kv_fwd_bwd_ex on HOST buffers: a->v, a->x, a->logk, a->dv and a->dx are host pointers; every
+ * other field means what it means for kv_fwd_bwd_ex, except that grad_out, status,
+ * fallback_count and the second-derivative outputs must be NULL (else KV_ERR_ARG), as must be a
+ * `transfer` outside enum kv_host_transfer.  Returns when the host outputs are complete (the call
+ * synchronizes a->stream). */
+int kv_fwd_bwd_host_ex(const kv_args* a, int transfer);
+
+/* kv_fwd_bwd_host_ex(a, KV_HOST_AUTO). */
 int kv_fwd_bwd_host(const kv_args* a);
+
+/* 1 if the current device reaches host memory over a coherent link (the condition under which
+ * KV_HOST_AUTO picks DIRECT for device-addressable buffers), else 0. */
+int kv_host_direct_supported(void);
 
 /* ------------------------------------------------------------------ building blocks */
 

@@ -134,31 +134,31 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // phi(s) = e^s - 1 - s and phi(-s), and e^{+-s}.
-// |s| <= 1: even/odd Taylor parts of phi in z = s^2 (terms to s^12 and s^11; the rest is below
-// 3e-10 relative), a few FP32 ulps relative.
+// |s| <= 1: phi(+-s) = z (E(z) +- s O(z)) with z = s^2 and the even/odd parts
+//   E(z) = (cosh s - 1) / z = sum_{k>=1} z^{k-1}/(2k)!,  O(z) = (sinh s / s - 1) / z = sum_{k>=1} z^{k-1}/(2k+1)!,
+// each replaced by its degree-3 minimax polynomial on z in [0, 1] (Remez exchange; the script
+// minimax_coeffs.py beside this file prints the coefficients): absolute errors 2.2e-9 (E, about
+// 0.5) and 2.0e-10 (O, about 1/6), below FP32 rounding, where the Taylor polynomials of the same
+// degree leave 2.8e-7 and 2.5e-8.
 // |s| > 1: from e^s = 2^{s log2 e} (ex2.approx: relative error about 2^-22 plus the rounding of
 // s log2 e, |s| 2^-24 relative), where the cancellation in e^s - 1 - s costs at most a few ulps of
 // e (phi(1) = 0.718, phi(-1) = 0.368: relative error below 1e-6 at |s| = 1, falling beyond).  The
 // weight of such a bin is exp(-(x e^{t_p}/2) phi(s) - ...), so the absolute error this leaves in
 // its exponent stays below 1e-6 wherever the bin's weight is not negligible.
 // Both forms are computed and the valid one is selected: lanes of a warp whose bins straddle
-// |s| = 1 would otherwise run both sides one after the other.  (The series at |s| > 1 is
+// |s| = 1 would otherwise run both sides one after the other.  (The polynomial at |s| > 1 is
 // discarded; it stays finite far beyond any range the bins cover, and an overflow there would
 // not reach the selected value.)  e^{+-s} themselves (for cosh t in the d/dx integrand, which
 // needs only FP32 relative accuracy) always come from ex2 and its reciprocal.
 constexpr float PHI_SERIES_MAX = 1.0f;
 
-// E(z) = sum_{k>=1} z^{k-1}/(2k)!,  O(z) = sum_{k>=1} z^{k-1}/(2k+1)!  for z <= 1
-#define KV_PHI_SERIES(MUL, FMA, C, z, E, O)                 \
-    E = FMA(C(1.0f / 479001600.0f), z, C(1.0f / 3628800.0f)); \
-    E = FMA(E, z, C(1.0f / 40320.0f));                        \
-    E = FMA(E, z, C(1.0f / 720.0f));                          \
-    E = FMA(E, z, C(1.0f / 24.0f));                           \
-    E = FMA(E, z, C(0.5f));                                   \
-    O = FMA(C(1.0f / 39916800.0f), z, C(1.0f / 362880.0f));   \
-    O = FMA(O, z, C(1.0f / 5040.0f));                         \
-    O = FMA(O, z, C(1.0f / 120.0f));                          \
-    O = FMA(O, z, C(1.0f / 6.0f));
+#define KV_PHI_SERIES(MUL, FMA, C, z, E, O)                        \
+    E = FMA(C(2.5358777544656039e-5f), z, C(1.3885392932591772e-3f)); \
+    E = FMA(E, z, C(4.1666736744439945e-2f));                        \
+    E = FMA(E, z, C(0.5f));                                          \
+    O = FMA(C(2.8063006223552967e-6f), z, C(1.9838098914288133e-4f)); \
+    O = FMA(O, z, C(8.3333396873695536e-3f));                        \
+    O = FMA(O, z, C(0.16666666646778531f));
 
 __device__ __forceinline__ float f1(float a) { return a; }
 
@@ -176,18 +176,21 @@ __device__ __forceinline__ void phi_pair(float s, float& php, float& phm, float&
     phm = small ? pm : (ems - 1.0f) + s;
 }
 
-// tanh(y) for |y| < 0.35 by its Taylor series through y^13 (relative error < 1e-9 there);
+// tanh(y) for |y| < 0.35 as y + y^3 P(y^2), P the degree-3 minimax polynomial of
+// (tanh(y)/y - 1)/y^2 on y^2 in [0, 0.35^2] (absolute error 1.4e-8 in P, so tanh's relative
+// error is below 2e-9 before FP32 rounding; coefficients from minimax_coeffs.py);
 // (1 - e^{-2y}) / (1 + e^{-2y}) loses relative precision to the cancellation in 1 - e^{-2y}
 // (about 2^-22 / (2y) relative: below 4e-7 from y = 0.35 on).
+#define KV_TANH_POLY(FMA, C, z, p)                      \
+    p = FMA(C(1.9843806701481164e-2f), z, C(-5.3817014230769577e-2f)); \
+    p = FMA(p, z, C(0.1333296820144401f));             \
+    p = FMA(p, z, C(-0.33333331952545429f));
+
 __device__ __forceinline__ float tanh_small(float y)
 {
-    float z = y * y;
-    float p = 21844.0f / 6081075.0f;
-    p = fmaf(p, z, -1382.0f / 155925.0f);
-    p = fmaf(p, z, 62.0f / 2835.0f);
-    p = fmaf(p, z, -17.0f / 315.0f);
-    p = fmaf(p, z, 2.0f / 15.0f);
-    p = fmaf(p, z, -1.0f / 3.0f);
+    const float z = y * y;
+    float p;
+    KV_TANH_POLY(fmaf, f1, z, p)
     return fmaf(y * z, p, y);
 }
 
@@ -214,12 +217,20 @@ __device__ __forceinline__ float delta_g_slope_f32(const BinsF& b, float e2, flo
     return b.c1 + dl - b.ap * (es - 1.0f) + b.am * (ems - 1.0f);
 }
 
-// The bin constants rescaled once per pair so that a bin works in base-2 exponent units: the
-// weight's exponent (g(t) - g(t_p)) log2 e goes straight into ex2.
+// The bin constants rescaled once per pair so that a bin works in base-2 exponent units.  The
+// weight is split as
+//   e^{g(t) - g(t_p)} = e^{-lu} (1 + e^{-2vt}) 2^{c1 s + N(s)},   lu = log1p(e^{-2u}),
+// with c1 = (v - x sinh t_p) log2 e and N(s) = -((x e^{t_p}/2) phi(s) + (x e^{-t_p}/2) phi(-s)) log2 e,
+// so that log1p(e^{-2vt}) is never taken (its exponential is the factor 1 + e^{-2vt}) and the
+// tanh integrand needs no reciprocal: w tanh(vt) = e^{-lu} (1 - e^{-2vt}) 2^{c1 s + N(s)}.
 struct BinsK {
     float c1, ap, am, lu;  // v - x sinh t_p, x e^{+-t_p}/2, log1p(e^{-2u}), each times log2 e
     float hep, hem;        // e^{+-t_p} / 2
-    float cA, cB, lA;      // x cosh t_p, x sinh t_p and log1p(e^{-2u}) - x cosh t_p, times log2 e
+    float cA, cB;          // x cosh t_p, x sinh t_p, times log2 e
+    float nA, nB;          // -cA, -cB
+    float nap, nam;        // -ap, -am
+    float nv2, nu2;        // -2 v log2 e, -2 u log2 e: e^{-2vt} = 2^{nv2 s + nu2}
+    float kc;              // e^{-lu} = 1 / (1 + e^{-2u})
 };
 
 __device__ __forceinline__ BinsK bins_k(const BinsF& b)
@@ -233,27 +244,32 @@ __device__ __forceinline__ BinsK bins_k(const BinsF& b)
     k.hem = 0.5f * b.em;
     k.cA = b.xch * LOG2E_F;
     k.cB = b.xsh * LOG2E_F;
-    k.lA = (b.lu - b.xch) * LOG2E_F;
+    k.nA = -k.cA;
+    k.nB = -k.cB;
+    k.nap = -k.ap;
+    k.nam = -k.am;
+    k.nv2 = -2.0f * LOG2E_F * b.v;
+    k.nu2 = -2.0f * LOG2E_F * b.u;
+    k.kc = ex2_approx(-k.lu);  // e^{-lu} from the same lu as the offset g(t_p), which it cancels
     return k;
 }
 
-// The x-part of the exponent plus the log1p offset, X = (x e^{t_p}/2) phi(s) + (x e^{-t_p}/2) phi(-s)
-// + log1p(e^{-2u}) (times log2 e), for two bins:
-//   |s| <= 1: phi(+-s) = z (E(z) +- s O(z)), so X = z (x cosh t_p E + x sinh t_p s O) + lu;
-//   |s| > 1:  X = (x e^{t_p}/2) e^s + (x e^{-t_p}/2) e^{-s} - x sinh t_p s + lu - x cosh t_p;
-// e^{+-s} (es, ems) are returned for the cosh t integrand.
+// N(s) for two bins:
+//   |s| <= 1: phi(+-s) = z (E(z) +- s O(z)), so N = -z (x cosh t_p E + x sinh t_p s O);
+//   |s| > 1:  N = -(x e^{t_p}/2) e^s - (x e^{-t_p}/2) e^{-s} + x sinh t_p s + x cosh t_p;
+// (all times log2 e); e^{+-s} (es, ems) are returned for the cosh t integrand.
 __device__ __forceinline__ float2 x_part2(const BinsK& k, float2 s, float2& es, float2& ems)
 {
     const float2 z = mul2(s, s);
     float2 E, O;
     KV_PHI_SERIES(mul2, fma2, f2, z, E, O)
     const float2 so = mul2(s, O);
-    const float2 xs = fma2(z, fma2(f2(k.cA), E, mul2(f2(k.cB), so)), f2(k.lu));
+    const float2 ns = mul2(z, fma2(f2(k.nA), E, mul2(f2(k.nB), so)));
     const float2 el = mul2(s, f2(LOG2E_F));
     es = make_float2(ex2_approx(el.x), ex2_approx(el.y));
     ems = make_float2(rcp_approx(es.x), rcp_approx(es.y));
-    const float2 xl = fma2(f2(k.ap), es, fma2(f2(k.am), ems, fma2(f2(-k.cB), s, f2(k.lA))));
-    return make_float2(fabsf(s.x) <= PHI_SERIES_MAX ? xs.x : xl.x, fabsf(s.y) <= PHI_SERIES_MAX ? xs.y : xl.y);
+    const float2 nl = fma2(f2(k.nap), es, fma2(f2(k.nam), ems, fma2(f2(k.cB), s, f2(k.cA))));
+    return make_float2(fabsf(s.x) <= PHI_SERIES_MAX ? ns.x : nl.x, fabsf(s.y) <= PHI_SERIES_MAX ? ns.y : nl.y);
 }
 
 __device__ __forceinline__ float x_part(const BinsK& k, float s, float& es, float& ems)
@@ -261,38 +277,40 @@ __device__ __forceinline__ float x_part(const BinsK& k, float s, float& es, floa
     const float z = s * s;
     float E, O;
     KV_PHI_SERIES(__fmul_rn, fmaf, f1, z, E, O)
-    const float xs = fmaf(z, fmaf(k.cA, E, k.cB * (s * O)), k.lu);
+    const float ns = z * fmaf(k.nA, E, k.nB * (s * O));
     es = ex2_approx(s * LOG2E_F);
     ems = rcp_approx(es);
-    const float xl = fmaf(k.ap, es, fmaf(k.am, ems, fmaf(-k.cB, s, k.lA)));
-    return fabsf(s) <= PHI_SERIES_MAX ? xs : xl;
+    const float nl = fmaf(k.nap, es, fmaf(k.nam, ems, fmaf(k.cB, s, k.cA)));
+    return fabsf(s) <= PHI_SERIES_MAX ? ns : nl;
 }
 
-// vt below this uses tanh_small
+// vt below this uses tanh_small; in the bins the test is on -2 vt log2 e (EA_SERIES_MIN)
 constexpr float TANH_SERIES_MAX = 0.35f;
+constexpr float EA_SERIES_MIN = -2.0f * LOG2E_F * TANH_SERIES_MAX;
 
 // One FP32 bin at m = mf (a float holding a small integer, exact): its weight c e^{g(t_m) - g(t_p)}
-// and the two derivative integrands' weights.  With VOTE (all 32 lanes of the warp run the same
-// bins together) the series for tanh(vt) is evaluated only when some lane of the warp needs it.
+// and the two derivative integrands' weights.  `ck` is c e^{-lu}.  With VOTE (all 32 lanes of the
+// warp run the same bins together) the series for tanh(vt) is evaluated only when some lane of
+// the warp needs it.
 template <bool DERIV, bool VOTE>
-__device__ __forceinline__ void bin_f32(const BinsF& b, const BinsK& k, float mf, float c, float& w,
+__device__ __forceinline__ void bin_f32(const BinsF& b, const BinsK& k, float mf, float ck, float& w,
                                         float& w1, float& w2)
 {
     const float s = fmaf(mf, b.h, b.s0);
     float es, ems;
-    const float X = x_part(k, s, es, ems);
-    const float vt = fmaf(b.v, s, b.u);
-    const float e2 = ex2_approx(-2.0f * LOG2E_F * vt);  // e^{-2vt}
-    // (g(t) - g(t_p)) log2 e with log1p(e^{-2vt}) - log1p(e^{-2u}) as lg2(1 + e2) - lu
-    const float dg = fmaf(k.c1, s, lg2_approx(1.0f + e2)) - X;
-    w = c * ex2_approx(dg);
+    const float N = x_part(k, s, es, ems);
+    const float ea = fmaf(k.nv2, s, k.nu2);
+    const float e2 = ex2_approx(ea);  // e^{-2vt}
+    const float ope = 1.0f + e2;
+    const float wp = ck * ex2_approx(fmaf(k.c1, s, N));
+    w = wp * ope;
     if (DERIV) {
         const float t = b.tp + s;
-        float th = (1.0f - e2) * rcp_approx(1.0f + e2);  // tanh(vt)
-        const bool small = vt < TANH_SERIES_MAX;
+        float q = 1.0f - e2;  // (1 + e^{-2vt}) tanh(vt)
+        const bool small = ea > EA_SERIES_MIN;
         if (!VOTE || __any_sync(0xffffffffu, small))
-            th = small ? tanh_small(vt) : th;
-        w1 = w * (t * th);
+            q = small ? tanh_small(ea * (-0.5f * LN2_F)) * ope : q;
+        w1 = wp * (t * q);
         w2 = w * fmaf(k.hep, es, k.hem * ems);  // w cosh t
     }
 }
@@ -302,39 +320,34 @@ __device__ __forceinline__ void bin_f32(const BinsF& b, const BinsK& k, float mf
 __device__ __forceinline__ float2 tanh_small2(float2 y)
 {
     const float2 z = mul2(y, y);
-    float2 p = f2(21844.0f / 6081075.0f);
-    p = fma2(p, z, f2(-1382.0f / 155925.0f));
-    p = fma2(p, z, f2(62.0f / 2835.0f));
-    p = fma2(p, z, f2(-17.0f / 315.0f));
-    p = fma2(p, z, f2(2.0f / 15.0f));
-    p = fma2(p, z, f2(-1.0f / 3.0f));
+    float2 p;
+    KV_TANH_POLY(fma2, f2, z, p)
     return fma2(mul2(y, z), p, y);
 }
 
-// bin_f32 for the two bins m = mf.x and mf.y; c0 is the weight factor of the first of them.
+// bin_f32 for the two bins m = mf.x and mf.y; ck.x and ck.y are their factors c e^{-lu}.
 template <bool DERIV, bool VOTE>
-__device__ __forceinline__ void bin_f32x2(const BinsF& b, const BinsK& k, float2 mf, float c0, float2& w,
+__device__ __forceinline__ void bin_f32x2(const BinsF& b, const BinsK& k, float2 mf, float2 ck, float2& w,
                                           float2& w1, float2& w2)
 {
     const float2 s = fma2(mf, f2(b.h), f2(b.s0));
     float2 es, ems;
-    const float2 X = x_part2(k, s, es, ems);
-    const float2 vt = fma2(f2(b.v), s, f2(b.u));
-    const float2 ea = mul2(vt, f2(-2.0f * LOG2E_F));
+    const float2 N = x_part2(k, s, es, ems);
+    const float2 ea = fma2(f2(k.nv2), s, f2(k.nu2));
     const float2 e2 = make_float2(ex2_approx(ea.x), ex2_approx(ea.y));  // e^{-2vt}
     const float2 ope = add2(f2(1.0f), e2);
-    const float2 lg = make_float2(lg2_approx(ope.x), lg2_approx(ope.y));
-    const float2 dg = sub2(fma2(f2(k.c1), s, lg), X);
-    w = make_float2(c0 * ex2_approx(dg.x), ex2_approx(dg.y));
+    const float2 dg = fma2(f2(k.c1), s, N);
+    const float2 wp = mul2(ck, make_float2(ex2_approx(dg.x), ex2_approx(dg.y)));
+    w = mul2(wp, ope);
     if (DERIV) {
         const float2 t = add2(f2(b.tp), s);
-        float2 th = mul2(sub2(f2(1.0f), e2), make_float2(rcp_approx(ope.x), rcp_approx(ope.y)));  // tanh(vt)
-        const bool kx = vt.x < TANH_SERIES_MAX, ky = vt.y < TANH_SERIES_MAX;
+        float2 q = sub2(f2(1.0f), e2);  // (1 + e^{-2vt}) tanh(vt)
+        const bool kx = ea.x > EA_SERIES_MIN, ky = ea.y > EA_SERIES_MIN;
         if (!VOTE || __any_sync(0xffffffffu, kx || ky)) {
-            const float2 ts = tanh_small2(vt);
-            th = make_float2(kx ? ts.x : th.x, ky ? ts.y : th.y);
+            const float2 tq = mul2(tanh_small2(mul2(ea, f2(-0.5f * LN2_F))), ope);  // vt from ea
+            q = make_float2(kx ? tq.x : q.x, ky ? tq.y : q.y);
         }
-        w1 = mul2(w, mul2(t, th));
+        w1 = mul2(wp, mul2(t, q));
         w2 = mul2(w, fma2(f2(k.hep), es, mul2(f2(k.hem), ems)));  // w cosh t
     }
 }
@@ -356,14 +369,14 @@ __device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, fl
     k2.init();
     int m = lane;
     float mf = (float)lane;
-    float c_first = lane == 0 ? 0.5f : 1.0f;
+    float c_first = lane == 0 ? 0.5f * k.kc : k.kc;
     for (; m + 3 * L < b.n; m += 4 * L, mf += (float)(4 * L)) {
         // bins m, m + L in one float2 and m + 2L, m + 3L in another; the block's four terms are
         // added pairwise, (w_m + w_{m+2L}) + (w_{m+L} + w_{m+3L}), and the sum goes to Kahan
         float2 wa, w1a, w2a, wb, w1b, w2b;
-        bin_f32x2<DERIV, VOTE>(b, k, make_float2(mf, mf + (float)L), c_first, wa, w1a, w2a);
-        bin_f32x2<DERIV, VOTE>(b, k, make_float2(mf + (float)(2 * L), mf + (float)(3 * L)), 1.0f, wb, w1b, w2b);
-        c_first = 1.0f;
+        bin_f32x2<DERIV, VOTE>(b, k, make_float2(mf, mf + (float)L), make_float2(c_first, k.kc), wa, w1a, w2a);
+        bin_f32x2<DERIV, VOTE>(b, k, make_float2(mf + (float)(2 * L), mf + (float)(3 * L)), f2(k.kc), wb, w1b, w2b);
+        c_first = k.kc;
         const float2 p0 = add2(wa, wb);
         k0.add(p0.x + p0.y);
         if (DERIV) {
@@ -374,7 +387,7 @@ __device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, fl
     }
     for (; m <= b.n; m += L, mf += (float)L) {
         float w, w1, w2;
-        bin_f32<DERIV, VOTE>(b, k, mf, (m == 0 || m == b.n) ? 0.5f : 1.0f, w, w1, w2);
+        bin_f32<DERIV, VOTE>(b, k, mf, (m == 0 || m == b.n) ? 0.5f * k.kc : k.kc, w, w1, w2);
         k0.add(w);
         if (DERIV) {
             k1.add(w1);

@@ -703,20 +703,111 @@ int kv_sum(const void* a, int64_t n, int dtype, double* out, void* stream)
     return KV_OK;
 }
 
-// Host-buffer form: chunks rotate over KV_HOST_SLOTS device buffer slots; one internal stream
-// copies inputs in, one copies outputs out and one per slot runs the kernels, ordered by events,
-// so one chunk's input copy, other chunks' kernels and another's output copy run at the same
-// time.  Device buffers (and the learned path's fallback lists) are allocated once per call.
-int kv_fwd_bwd_host(const kv_args* h)
+}  // extern "C"
+
+namespace {
+
+// The device address of host buffer [p, p + bytes) when the whole range is page-locked host
+// memory mapped into the device's address space (both ends are checked, and they must map
+// contiguously), else nullptr.  Never leaves a CUDA error behind.
+void* host_device_alias(const void* p, size_t bytes)
+{
+    if (!p || bytes == 0) return nullptr;
+    cudaPointerAttributes a0, a1;
+    const char* last = (const char*)p + (bytes - 1);
+    const bool ok = cudaPointerGetAttributes(&a0, p) == cudaSuccess &&
+                    cudaPointerGetAttributes(&a1, last) == cudaSuccess && a0.type == cudaMemoryTypeHost &&
+                    a1.type == cudaMemoryTypeHost && a0.devicePointer && a1.devicePointer &&
+                    (const char*)a1.devicePointer == (const char*)a0.devicePointer + (bytes - 1);
+    cudaGetLastError();
+    return ok ? a0.devicePointer : nullptr;
+}
+
+// Whether the current device reaches host memory over a coherent link (native host atomics or
+// access through the host's page tables, as on NVLink-C2C systems), where kernels reading and
+// writing host buffers directly keep up with the fused kernel.
+bool coherent_host_link()
+{
+    static int cache[64];
+    static bool known[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return false;
+    }
+    if (!known[dev]) {
+        int atomics = 0, host_tables = 0;
+        cudaDeviceGetAttribute(&atomics, cudaDevAttrHostNativeAtomicSupported, dev);
+        cudaDeviceGetAttribute(&host_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev);
+        cudaGetLastError();
+        cache[dev] = (atomics == 1 || host_tables == 1) ? 1 : 0;
+        known[dev] = true;
+    }
+    return cache[dev] == 1;
+}
+
+// DIRECT transfer: one launch of the path on the host buffers' device aliases, on the caller's
+// stream; the fallback list is device memory allocated on the stream.
+int host_direct(const kv_args* h, void* const alias[5])
+{
+    kv_args d = *h;
+    d.v = alias[0];
+    d.x = alias[1];
+    d.logk = alias[2];
+    d.dv = alias[3];
+    d.dx = alias[4];
+    int rc = kvh::fwd_bwd_ex(&d, nullptr);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)h->stream);
+    if (rc != KV_OK) return rc;
+    if (e != cudaSuccess) return kvh::cuda_fail(e);
+    return KV_OK;
+}
+
+int host_staged(const kv_args* h);
+
+}  // namespace
+
+extern "C" {
+
+int kv_host_direct_supported(void) { return coherent_host_link() ? 1 : 0; }
+
+int kv_fwd_bwd_host_ex(const kv_args* h, int transfer)
 {
     if (!h) return KV_ERR_NULL;
     if (h->grad_out || h->status || h->fallback_count || h->d2v || h->dvx || h->d2x) return KV_ERR_ARG;
+    if (transfer != KV_HOST_AUTO && transfer != KV_HOST_STAGED && transfer != KV_HOST_DIRECT) return KV_ERR_ARG;
     int bins_, max_iter_, lanes_;
     double log_eps_;
     int rc = validate(h, &bins_, &log_eps_, &max_iter_, &lanes_);
     if (rc != KV_OK) return rc;
+    if (h->n == 0) return KV_OK;
+    if (transfer != KV_HOST_STAGED) {
+        const size_t bytes = kvh::elem_size(h->dtype) * (size_t)h->n;
+        const void* host[5] = {h->v, h->x, h->logk, h->dv, h->dx};
+        void* alias[5] = {};
+        bool all = true;
+        for (int k = 0; k < 5; ++k)
+            if (host[k] && !(alias[k] = host_device_alias(host[k], bytes))) all = false;
+        if (transfer == KV_HOST_DIRECT && !all) return KV_ERR_ARG;
+        if (all && (transfer == KV_HOST_DIRECT || coherent_host_link())) return host_direct(h, alias);
+    }
+    return host_staged(h);
+}
+
+int kv_fwd_bwd_host(const kv_args* h) { return kv_fwd_bwd_host_ex(h, KV_HOST_AUTO); }
+
+}  // extern "C"
+
+namespace {
+
+// STAGED transfer: chunks rotate over KV_HOST_SLOTS device buffer slots; one internal stream
+// copies inputs in, one copies outputs out and one per slot runs the kernels, ordered by events,
+// so one chunk's input copy, other chunks' kernels and another's output copy run at the same
+// time.  Device buffers (and the learned path's fallback lists) are allocated once per call.
+int host_staged(const kv_args* h)
+{
+    int rc = KV_OK;
     const int64_t n = h->n;
-    if (n == 0) return KV_OK;
     const size_t es = kvh::elem_size(h->dtype);
     // chunk sizes: doubling from the minimum at the start and halving towards the end (short
     // fill and drain of the pipeline), the maximum in between (few launches)
@@ -836,6 +927,10 @@ int kv_fwd_bwd_host(const kv_args* h)
     if (e != cudaSuccess) return kvh::cuda_fail(e);
     return KV_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 const char* kv_strerror(int code)
 {

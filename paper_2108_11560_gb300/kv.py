@@ -125,10 +125,16 @@ def kv_fwd_bwd_ex(v, x, *, bins: int = 0, bracket: str = "plain", log_eps: float
     return out
 
 
+HOST_TRANSFER = {"auto": N.KV_HOST_AUTO, "staged": N.KV_HOST_STAGED, "direct": N.KV_HOST_DIRECT}
+
+
 def kv_fwd_bwd_host(v, x, *, bins: int = 0, bracket: str = "plain", mlp=None, log_eps: float = 0.0,
-                    out=None):
-    """kv_fwd_bwd_ex on host numpy arrays (pinned memory gives full copy speed): copies to the
-    device and back inside the call.  Returns (logk, dv, dx) numpy arrays."""
+                    out=None, transfer: str = "auto"):
+    """kv_fwd_bwd_ex on host numpy arrays; returns (logk, dv, dx) numpy arrays.  `transfer`:
+    "staged" copies through device buffers (any host memory; pinned gives full copy speed),
+    "direct" lets the kernels read and write the host buffers in place (all five must be pinned
+    and mapped, e.g. numpy views of torch pin_memory() tensors), "auto" takes "direct" for such
+    buffers on a coherent CPU-GPU link (see host_direct_supported) and "staged" otherwise."""
     import numpy as np
     v = np.ascontiguousarray(v)
     x = np.ascontiguousarray(x)
@@ -140,6 +146,8 @@ def kv_fwd_bwd_host(v, x, *, bins: int = 0, bracket: str = "plain", mlp=None, lo
         dt = N.KV_MIXED
     else:
         raise TypeError("host arrays must be float64 or float32")
+    if transfer not in HOST_TRANSFER:
+        raise ValueError(f"transfer must be one of {sorted(HOST_TRANSFER)}")
     if out is None:
         out = tuple(np.empty_like(v) for _ in range(3))
     lk, dv, dx = out
@@ -153,8 +161,14 @@ def kv_fwd_bwd_host(v, x, *, bins: int = 0, bracket: str = "plain", mlp=None, lo
     a.log_eps = log_eps
     a.mlp = mlp.handle if mlp is not None else None
     a.stream = _stream_ptr(torch.device("cuda", torch.cuda.current_device()))
-    N.check(N.lib().kv_fwd_bwd_host(ctypes.byref(a)), "kv_fwd_bwd_host")
+    N.check(N.lib().kv_fwd_bwd_host_ex(ctypes.byref(a), HOST_TRANSFER[transfer]), "kv_fwd_bwd_host_ex")
     return lk, dv, dx
+
+
+def host_direct_supported() -> bool:
+    """Whether the current GPU reaches host memory over a coherent link (NVLink-C2C class), the
+    condition under which transfer="auto" reads and writes pinned host buffers in place."""
+    return bool(N.lib().kv_host_direct_supported())
 
 
 def kv_bracket(v, x, log_eps: float = 0.0, max_iter: int = 0):

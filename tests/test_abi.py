@@ -81,6 +81,10 @@ def test_host_side_argument_errors(lib):
     a.bins = 0
     a.status = 256
     assert lib.kv_fwd_bwd_host(ctypes.byref(a)) == -7
+    a.status = None
+    assert lib.kv_fwd_bwd_host_ex(ctypes.byref(a), 3) == -7  # no such transfer mode
+    assert lib.kv_fwd_bwd_host_ex(ctypes.byref(a), -1) == -7
+    assert lib.kv_fwd_bwd_host_ex(None, 0) == -1
 
 
 def test_second_derivative_argument_errors(lib):

@@ -14,7 +14,7 @@ if not torch.cuda.is_available():
 
 import oracle
 from conftest import rel, rel_logk
-from paper_2108_11560_gb300 import kv
+from paper_2108_11560_gb300 import kv, learned
 from paper_2108_11560_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -191,15 +191,49 @@ def test_full_size_hard_band_sampled():
     assert rel(_np(dx)[idx[:1024]], truth["dx"]).max() < TOL_MIXED
 
 
-def test_host_buffer_call_matches_device_call():
+def _pinned(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+
+@pytest.mark.parametrize("transfer,pinned", [("auto", False), ("staged", True), ("direct", True), ("auto", True)])
+def test_host_buffer_call_matches_device_call(transfer, pinned):
+    # pageable buffers take the staged copies; pinned ones either transfer, so every route must
+    # give the device call's results bit for bit
     v, x = W.hard_band(5_000_000, seed=211)
     vf = v.astype(np.float32)
     xf = x.astype(np.float32)
-    lk_h, dv_h, dx_h = kv.kv_fwd_bwd_host(vf, xf, bins=32)
+    hv, hx = (_pinned(vf), _pinned(xf)) if pinned else (vf, xf)
+    out = tuple(_pinned(np.zeros_like(vf)) if pinned else np.zeros_like(vf) for _ in range(3))
+    lk_h, dv_h, dx_h = kv.kv_fwd_bwd_host(hv, hx, bins=32, out=out, transfer=transfer)
     lk, dv, dx = kv.kv_fwd_bwd(_t(vf, torch.float32), _t(xf, torch.float32), bins=32)
     assert np.array_equal(lk_h, lk.cpu().numpy())
     assert np.array_equal(dv_h, dv.cpu().numpy())
     assert np.array_equal(dx_h, dx.cpu().numpy())
+
+
+def test_host_buffer_call_learned_path_direct():
+    # the fast path (with its fallback list in device memory) on pinned host buffers in place
+    net = learned.default_network(torch.device("cuda", 0))
+    v, x = W.hard_band(3_000_001, seed=213)
+    vf, xf = v.astype(np.float32), x.astype(np.float32)
+    out = tuple(_pinned(np.zeros_like(vf)) for _ in range(3))
+    lk_h, dv_h, dx_h = kv.kv_fwd_bwd_host(_pinned(vf), _pinned(xf), bins=32, bracket="mlp", mlp=net,
+                                          out=out, transfer="direct")
+    r = kv.kv_fwd_bwd_ex(_t(vf, torch.float32), _t(xf, torch.float32), bins=32, bracket="mlp", mlp=net)
+    assert np.array_equal(lk_h, r["logk"].cpu().numpy())
+    assert np.array_equal(dv_h, r["dv"].cpu().numpy())
+    assert np.array_equal(dx_h, r["dx"].cpu().numpy())
+
+
+def test_host_direct_rejects_unpinned_buffers():
+    # the check runs on the host before any launch: pageable memory is not device-addressable
+    vf = np.linspace(0.5, 3.0, 1000, dtype=np.float32)
+    with pytest.raises(RuntimeError):
+        kv.kv_fwd_bwd_host(vf, vf.copy(), bins=32, transfer="direct")
+    # one pinned and one pageable input: rejected as well
+    with pytest.raises(RuntimeError):
+        kv.kv_fwd_bwd_host(_pinned(vf), vf.copy(), bins=32, transfer="direct")
+    assert kv.host_direct_supported() in (True, False)
 
 
 # ------------------------------------------------------------------ reductions and autograd
