@@ -18,6 +18,11 @@
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls are
  *     asynchronous on that stream; argument errors are detected on the host before any launch.
  *   - n == 0 is a valid no-op.  Output pointers may alias nothing else.
+ *   - Scratch device memory a call needs (the learned path's fallback list, 4 bytes per pair;
+ *     the host call's staging buffers; partial sums) is allocated stream-ordered on `stream` from
+ *     a memory pool of the library's own on the current device and freed to it before the call's
+ *     work ends.  The pool keeps freed memory reserved for later calls (a synchronizing call would
+ *     otherwise return it to the system and map it again each time); kv_trim_memory() releases it.
  *   - Return value: KV_OK (0) or a negative kv_status; kv_strerror() describes it.
  *
  * Per-pair domain results (no error code; Sec. 2 defines K for v real, x > 0):
@@ -151,8 +156,8 @@ enum kv_host_transfer {
     KV_HOST_AUTO = 0,
     /* Copies through device buffers: chunks of up to 2^19 pairs pipelined over four buffer
      * slots (internal streams for the copies in, the copies out and each slot's kernels, ordered
-     * by events and started after the work already on a->stream).  Device staging memory is
-     * allocated and freed on a->stream inside the call.  Any host memory; pinned
+     * by events and started after the work already on a->stream).  Device staging memory comes
+     * from the library's scratch pool on a->stream.  Any host memory; pinned
      * (cudaHostAlloc) for full copy speed. */
     KV_HOST_STAGED = 1,
     /* No staging copies: the kernels read v and x from, and write the outputs to, the host
@@ -160,7 +165,7 @@ enum kv_host_transfer {
      * mapped into the device's address space over its whole length (cudaHostAlloc /
      * cudaMallocHost under unified addressing, or cudaHostRegister with cudaHostRegisterMapped);
      * the call checks both ends of each buffer and returns KV_ERR_ARG otherwise, without
-     * launching anything.  The fallback list of the learned path is device memory allocated on
+     * launching anything.  The fallback list of the learned path is device scratch memory on
      * a->stream. */
     KV_HOST_DIRECT = 2
 };
@@ -203,7 +208,7 @@ int kv_grad2(const void* go, const void* gg_v, const void* gg_x, const void* dv,
 
 /* Deterministic sum of n elements (dtype's element type) into *out (one double, device memory).
  * Used for the log-likelihood sum_i log K(v_i, x_i).  Scratch memory for the per-block partial
- * sums is allocated and freed on `stream` (stream-ordered allocation). */
+ * sums comes from the library's scratch pool on `stream` (stream-ordered allocation). */
 int kv_sum(const void* a, int64_t n, int dtype, double* out, void* stream);
 
 /* The same deterministic sum for callers that cannot allocate device memory: applications whose
@@ -273,6 +278,10 @@ int kv_mlp_predict(const kv_mlp* h, const void* v, const void* x, void* t0, void
 /* ------------------------------------------------------------------ diagnostics */
 /* Number of kernels this library has launched in this process (all threads, all devices). */
 uint64_t kv_launch_count(void);
+
+/* Releases the device memory the library's scratch pool on the current device keeps reserved
+ * (cudaMemPoolTrimTo to 0; memory of calls still in flight stays).  KV_OK if there is no pool. */
+int kv_trim_memory(void);
 
 /* ------------------------------------------------------------------ errors */
 const char* kv_strerror(int code);

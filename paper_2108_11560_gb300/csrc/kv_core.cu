@@ -15,6 +15,7 @@
 #include "kv_internal.h"
 
 #include <atomic>
+#include <mutex>
 
 // The host-buffer entry point streams chunks of 2^KV_HOST_MIN_CHUNK_LOG2 up to
 // 2^KV_HOST_CHUNK_LOG2 pairs through KV_HOST_SLOTS device buffer slots.
@@ -43,6 +44,54 @@ int cuda_fail(cudaError_t e)
 }
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64];
+}  // namespace
+
+// The library's own stream-ordered pool on the current device, created on first use with a
+// release threshold that keeps freed memory reserved.
+static cudaError_t scratch_pool(cudaMemPool_t* out, bool create)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev] && create) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = ~(uint64_t)0;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t s)
+{
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = scratch_pool(&pool, true);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+cudaError_t scratch_free(void* p, cudaStream_t s) { return cudaFreeAsync(p, s); }
+
+cudaError_t scratch_pool_get(cudaMemPool_t* pool) { return scratch_pool(pool, false); }
 
 int sm_count()
 {
@@ -685,7 +734,7 @@ int kv_sum(const void* a, int64_t n, int dtype, double* out, void* stream)
     }
     int nb = sum_blocks(n);
     double* part = nullptr;
-    KV_CUDA_TRY(cudaMallocAsync((void**)&part, sizeof(double) * nb, s));
+    KV_CUDA_TRY(kvh::scratch_alloc((void**)&part, sizeof(double) * nb, s));
     if (dtype == KV_F64)
         kv_sum_partial<double><<<nb, kSumBlock, 0, s>>>((const double*)a, n, part);
     else
@@ -697,7 +746,7 @@ int kv_sum(const void* a, int64_t n, int dtype, double* out, void* stream)
         kvh::note_launch();
         e = cudaGetLastError();
     }
-    cudaError_t e2 = cudaFreeAsync(part, s);
+    cudaError_t e2 = kvh::scratch_free(part, s);
     if (e != cudaSuccess) return kvh::cuda_fail(e);
     if (e2 != cudaSuccess) return kvh::cuda_fail(e2);
     return KV_OK;
@@ -847,7 +896,7 @@ int host_staged(const kv_args* h)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&out_free[k], cudaEventDisableTiming);
     }
     char* buf = nullptr;
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&buf, slot_bytes * nslots, caller);
+    if (e == cudaSuccess) e = kvh::scratch_alloc((void**)&buf, slot_bytes * nslots, caller);
     // everything starts after the caller's stream has reached this call (and the allocation)
     if (e == cudaSuccess) e = cudaEventRecord(start, caller);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sin, start, 0);
@@ -909,7 +958,7 @@ int host_staged(const kv_args* h)
         if (e == cudaSuccess) e = e2;
     }
     if (buf) {
-        cudaError_t e2 = cudaFreeAsync(buf, caller);
+        cudaError_t e2 = kvh::scratch_free(buf, caller);
         if (e == cudaSuccess) e = e2;
     }
     cudaError_t e3 = cudaStreamSynchronize(caller);
@@ -954,5 +1003,14 @@ const char* kv_strerror(int code)
 const char* kv_last_cuda_error(void) { return g_last_cuda_error; }
 
 uint64_t kv_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int kv_trim_memory(void)
+{
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = kvh::scratch_pool_get(&pool);
+    if (e == cudaSuccess && pool) e = cudaMemPoolTrimTo(pool, 0);
+    if (e != cudaSuccess) return kvh::cuda_fail(e);
+    return KV_OK;
+}
 
 }  // extern "C"

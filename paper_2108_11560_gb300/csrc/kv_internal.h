@@ -13,6 +13,16 @@ int cuda_fail(cudaError_t e);
 // Number of SMs of the current device (cached per device).
 int sm_count();
 
+// Stream-ordered scratch memory (fallback lists, staging buffers, partial sums) from a pool of
+// the library's own on the current device.  Its release threshold keeps freed memory reserved
+// for the next call: a call that synchronizes (the host-buffer call) would otherwise see the
+// default pool hand its memory back at every synchronization and map it again on the next call.
+// kv_trim_memory() releases it.
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t s);
+cudaError_t scratch_free(void* p, cudaStream_t s);
+// The pool of the current device, or nullptr if none was created yet.
+cudaError_t scratch_pool_get(cudaMemPool_t* pool);
+
 inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 inline size_t elem_size(int dtype) { return dtype == KV_F64 ? 8 : 4; }

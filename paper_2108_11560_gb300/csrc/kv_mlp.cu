@@ -1209,7 +1209,7 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
     cudaStream_t s = (cudaStream_t)a->stream;
     // scratch: the fallback list and its counter (the caller's, or allocated on the stream)
     uint32_t* scratch = scratch_in;
-    if (!scratch) KV_CUDA_TRY(cudaMallocAsync((void**)&scratch, sizeof(uint32_t) * (a->n + 32), s));
+    if (!scratch) KV_CUDA_TRY(scratch_alloc((void**)&scratch, sizeof(uint32_t) * (a->n + 32), s));
     p.fb_count = scratch;
     p.fb_list = scratch + 32;
     cudaError_t e = cudaMemsetAsync(p.fb_count, 0, sizeof(uint32_t), s);
@@ -1252,7 +1252,7 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
         note_launch();
         e = cudaGetLastError();
     }
-    cudaError_t e2 = scratch_in ? cudaSuccess : cudaFreeAsync(scratch, s);
+    cudaError_t e2 = scratch_in ? cudaSuccess : scratch_free(scratch, s);
     if (e != cudaSuccess) return cuda_fail(e);
     if (e2 != cudaSuccess) return cuda_fail(e2);
     return KV_OK;
@@ -1395,7 +1395,7 @@ int kv_mlp_loss_grad(const kv_mlp* h, const double* v, const double* x, const do
     cudaStream_t s = (cudaStream_t)stream;
     const int nb = (int)((n + kTrainBlock - 1) / kTrainBlock);
     float* partial = nullptr;
-    KV_CUDA_TRY(cudaMallocAsync((void**)&partial, sizeof(float) * (size_t)nb * (NP + 1), s));
+    KV_CUDA_TRY(kvh::scratch_alloc((void**)&partial, sizeof(float) * (size_t)nb * (NP + 1), s));
     int rc = run_grad(h, v, x, t0, t1, n, (int)n, 0, 0, 1, partial, s);
     if (rc == KV_OK) {
         ReduceArgs r;
@@ -1410,7 +1410,7 @@ int kv_mlp_loss_grad(const kv_mlp* h, const double* v, const double* x, const do
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = kvh::cuda_fail(e);
     }
-    cudaError_t e2 = cudaFreeAsync(partial, s);
+    cudaError_t e2 = kvh::scratch_free(partial, s);
     if (rc == KV_OK && e2 != cudaSuccess) rc = kvh::cuda_fail(e2);
     return rc;
 }
@@ -1428,7 +1428,7 @@ int kv_mlp_train(kv_mlp* h, const kv_train_args* a)
     cudaStream_t s = (cudaStream_t)a->stream;
     const int nb = (a->batch + kTrainBlock - 1) / kTrainBlock;
     float* partial = nullptr;
-    KV_CUDA_TRY(cudaMallocAsync((void**)&partial, sizeof(float) * (size_t)nb * (NP + 1), s));
+    KV_CUDA_TRY(kvh::scratch_alloc((void**)&partial, sizeof(float) * (size_t)nb * (NP + 1), s));
     int rc = KV_OK;
     if (a->steps > 0) h->host_ok = false;  // the device copy moves on; refreshed at the next use
     for (int j = 0; j < a->steps && rc == KV_OK; ++j) {
@@ -1457,7 +1457,7 @@ int kv_mlp_train(kv_mlp* h, const kv_train_args* a)
         if (e != cudaSuccess) rc = kvh::cuda_fail(e);
         h->step = t;
     }
-    cudaError_t e2 = cudaFreeAsync(partial, s);
+    cudaError_t e2 = kvh::scratch_free(partial, s);
     if (rc == KV_OK && e2 != cudaSuccess) rc = kvh::cuda_fail(e2);
     return rc;
 }

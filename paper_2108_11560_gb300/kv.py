@@ -165,6 +165,11 @@ def kv_fwd_bwd_host(v, x, *, bins: int = 0, bracket: str = "plain", mlp=None, lo
     return lk, dv, dx
 
 
+def trim_memory() -> None:
+    """Release the device memory the library's scratch pool keeps reserved between calls."""
+    N.check(N.lib().kv_trim_memory(), "kv_trim_memory")
+
+
 def host_direct_supported() -> bool:
     """Whether the current GPU reaches host memory over a coherent link (NVLink-C2C class), the
     condition under which transfer="auto" reads and writes pinned host buffers in place."""

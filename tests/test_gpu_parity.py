@@ -236,6 +236,21 @@ def test_host_direct_rejects_unpinned_buffers():
     assert kv.host_direct_supported() in (True, False)
 
 
+def test_scratch_pool_trim_and_reuse():
+    # scratch memory is kept by the library's pool between calls; trimming releases it and the
+    # next call allocates again
+    v, x = W.hard_band(1 << 20, seed=214)
+    vt, xt = _t(v.astype(np.float32), torch.float32), _t(x.astype(np.float32), torch.float32)
+    net = learned.default_network(DEV)
+    r1 = kv.kv_fwd_bwd_ex(vt, xt, bins=32, bracket="mlp", mlp=net)
+    torch.cuda.synchronize()
+    kv.trim_memory()
+    r2 = kv.kv_fwd_bwd_ex(vt, xt, bins=32, bracket="mlp", mlp=net)
+    for k in ("logk", "dv", "dx"):
+        assert torch.equal(r1[k], r2[k])
+    kv.trim_memory()
+
+
 # ------------------------------------------------------------------ reductions and autograd
 
 def test_sum_is_deterministic_and_exact_enough():
