@@ -279,6 +279,15 @@ int kv_mlp_predict(const kv_mlp* h, const void* v, const void* x, void* t0, void
 /* Number of kernels this library has launched in this process (all threads, all devices). */
 uint64_t kv_launch_count(void);
 
+/* For tests of the failure path: sets the iteration limit of the learned fast path's bounded
+ * wait for its tensor-core results (each iteration one mbarrier try-wait).  A CTA whose wait runs
+ * out hands all its remaining pairs to the fallback pass (the plain bracket, FP32 then FP64; edge
+ * inputs get their edge results there), so the results stay correct, only slower; the CTA still
+ * waits, with the full default limit, for the tensor-core work in flight before it releases its
+ * tensor memory.  iterations >= 0 sets the limit (0: the wait gives up at once); < 0 restores the
+ * default (2^22).  Process-wide; returns the previous setting (-1 for the default). */
+int kv_debug_set_wait_limit(int iterations);
+
 /* Releases the device memory the library's scratch pool on the current device keeps reserved
  * (cudaMemPoolTrimTo to 0; memory of calls still in flight stays).  KV_OK if there is no pool. */
 int kv_trim_memory(void);

@@ -23,6 +23,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -361,6 +362,7 @@ struct MlpPathParams {
     uint32_t* fb_count;
     kvh::MlpView mlp;
     MlpConst wc;
+    int wait_limit;  // iterations of the per-tile wait for the tensor-core results
 };
 
 constexpr int kMlpBlock = 128;
@@ -495,10 +497,10 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar)
 
 // Waits (bounded) for the mbarrier phase `phase` to complete; false if the limit ran out.
 constexpr int kWaitLimit = 1 << 22;
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, int limit = kWaitLimit)
 {
     uint32_t done = 0;
-    for (int it = 0; it < kWaitLimit && !done; ++it)
+    for (int it = 0; it < limit && !done; ++it)
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
@@ -711,7 +713,7 @@ __global__ void __launch_bounds__(kMlpBlock, 8) kv_mlp_tc_kernel(MlpPathParams p
             mma_bf16(tmem, umma_desc(smem_addr(sm.ones), 128, 0), umma_desc(smem_addr(sm.bb), 128, 256), idesc2, 1);
             mma_commit(&sm.mbar);
         }
-        if (__syncthreads_or(!mbar_wait(&sm.mbar, phase))) {
+        if (__syncthreads_or(!mbar_wait(&sm.mbar, phase, p.wait_limit))) {
             aborted = true;
             break;
         }
@@ -754,7 +756,7 @@ __global__ void __launch_bounds__(kMlpBlock, 8) kv_mlp_tc_kernel(MlpPathParams p
                 p.fb_list[k] = (uint32_t)i;
             }
         }
-        mbar_wait(&sm.mbar, phase);  // let the MMA in flight finish before its TMEM goes (bounded)
+        mbar_wait(&sm.mbar, phase);  // let the MMA in flight finish before its TMEM goes (full bound)
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -818,6 +820,29 @@ __global__ void __launch_bounds__(kMlpBlock) kv_fallback_kernel(FallbackParams f
         atomicAdd(f.fallback_total, (unsigned long long)cnt);
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
         const int64_t i = p.fb_list[k];
+        {
+            // an edge pair is on the list only when a fast-path CTA gave up its tensor-core wait
+            // and handed over all its remaining pairs
+            float lk, dv, dx;
+            const float ve = p.v[i], xe = p.x[i];
+            if (float_edge(ve, xe, lk, dv, dx)) {
+                if (p.go) {
+                    dv *= p.go[i];
+                    dx *= p.go[i];
+                }
+                if (p.logk) p.logk[i] = lk;
+                if (p.dv) p.dv[i] = dv;
+                if (p.dx) p.dx[i] = dx;
+                if (p.status) p.status[i] = KV_PAIR_EDGE;
+                if constexpr (D2) {
+                    const float e = (isinf(xe) && xe > 0.0f) ? 0.0f : nanf("");
+                    if (p.d2v) p.d2v[i] = e;
+                    if (p.dvx) p.dvx[i] = e;
+                    if (p.d2x) p.d2x[i] = e;
+                }
+                continue;
+            }
+        }
         if (f.try_f32) {
             const float vf = p.v[i], xf = p.x[i];
             const float va = fabsf(vf);
@@ -1180,6 +1205,8 @@ int fill_mlp_const(const kv_mlp* hc, cudaStream_t s, MlpConst* c)
     return KV_OK;
 }
 
+std::atomic<int> g_wait_limit{-1};  // < 0: kWaitLimit
+
 int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, uint32_t* scratch_in)
 {
     if (a->n > (int64_t)0xffffffffll) return KV_ERR_SIZE;
@@ -1204,6 +1231,8 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
     p.bins = bins;
     p.inv_bins = 1.0f / (float)bins;
     p.log_eps = (float)log_eps;
+    const int wl = g_wait_limit.load(std::memory_order_relaxed);
+    p.wait_limit = wl < 0 ? kWaitLimit : wl;
     rc = ensure_exp_table();
     if (rc != KV_OK) return rc;
     cudaStream_t s = (cudaStream_t)a->stream;
@@ -1481,6 +1510,11 @@ int kv_mlp_predict(const kv_mlp* h, const void* v, const void* x, void* t0, void
                                                  (float*)t1, n);
     KV_LAUNCH_CHECK();
     return KV_OK;
+}
+
+int kv_debug_set_wait_limit(int iterations)
+{
+    return kvh::g_wait_limit.exchange(iterations < 0 ? -1 : iterations, std::memory_order_relaxed);
 }
 
 }  // extern "C"

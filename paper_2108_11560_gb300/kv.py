@@ -165,6 +165,13 @@ def kv_fwd_bwd_host(v, x, *, bins: int = 0, bracket: str = "plain", mlp=None, lo
     return lk, dv, dx
 
 
+def debug_set_wait_limit(iterations: int) -> int:
+    """Test hook for the fast path's failure handling: the iteration limit of its bounded wait for
+    the tensor-core results (0: give up at once, so every CTA hands its pairs to the fallback
+    pass; < 0: the default).  Returns the previous setting (-1 = default)."""
+    return int(N.lib().kv_debug_set_wait_limit(int(iterations)))
+
+
 def trim_memory() -> None:
     """Release the device memory the library's scratch pool keeps reserved between calls."""
     N.check(N.lib().kv_trim_memory(), "kv_trim_memory")

@@ -227,6 +227,58 @@ def test_mlp_path_edge_cases(net):
     assert np.all(st[:11] == N.KV_PAIR_EDGE) and not (st[11] & N.KV_PAIR_EDGE)
 
 
+@pytest.mark.parametrize("second", [False, True])
+def test_tensor_core_wait_running_out_falls_back(net, second):
+    """Failure handling of the fast path, with no fault: with the wait for the tensor-core results
+    limited to zero tries, every CTA gives up at its first tile and hands all its pairs, edge pairs
+    included, to the fallback pass.  The outputs must still match the oracle (edge pairs: exactly
+    what the normal call gives), every regular pair carries the fallback bit, and the next call
+    with the default limit runs normally on the same context."""
+    v1, x1 = W.hard_band(50_000, seed=316)
+    ve = np.array([1.0, 0.0, -2.0, 3.0, np.inf, 1.0, np.nan, 1.0, -2.5])
+    xe = np.array([0.0, 0.0, np.inf, np.inf, 1.0, -1.0, 1.0, np.nan, 3.0])
+    v = np.concatenate([v1[:25_000], ve, v1[25_000:]])
+    x = np.concatenate([x1[:25_000], xe, x1[25_000:]])
+    (vf, v64), (xf, x64) = W.to_f32(v, x)
+    edge = np.isnan(vf) | np.isnan(xf) | (xf <= 0) | np.isinf(xf) | np.isinf(vf)
+    vt, xt = _t(vf, torch.float32), _t(xf, torch.float32)
+    fb = torch.zeros(1, dtype=torch.int64, device=DEV)
+    prev = kv.debug_set_wait_limit(0)
+    try:
+        out = kv.kv_fwd_bwd_ex(vt, xt, bins=40, bracket="mlp", mlp=net, status=True, fallback_count=fb,
+                               second=second)
+        torch.cuda.synchronize()
+    finally:
+        kv.debug_set_wait_limit(prev)
+    assert prev == -1
+    st = out["status"].cpu().numpy()
+    assert np.all(st[edge] == N.KV_PAIR_EDGE)
+    assert np.all(st[~edge] & N.KV_PAIR_FALLBACK)
+    assert fb.item() == v.size  # every pair was handed over
+    fb2 = torch.zeros(1, dtype=torch.int64, device=DEV)
+    normal = kv.kv_fwd_bwd_ex(vt, xt, bins=40, bracket="mlp", mlp=net, status=True, fallback_count=fb2,
+                              second=second)
+    assert fb2.item() < 0.02 * v.size
+    keys = ("logk", "dv", "dx") + (("d2v", "dvx", "d2x") if second else ())
+    for k in keys:
+        assert np.array_equal(_np(out[k])[edge], _np(normal[k])[edge], equal_nan=True), k
+    fin = ~edge
+    ref = oracle.o1(v64[fin], x64[fin], bins=40, log_eps=LOG_EPS, precision="long", second=second)
+    assert rel_logk(_np(out["logk"])[fin], ref["logk"]).max() < TOL
+    dv = _np(out["dv"])[fin]
+    z = v64[fin] == 0
+    assert np.all(dv[z] == 0)
+    assert rel(dv[~z], ref["dv"][~z]).max() < TOL
+    assert rel(_np(out["dx"])[fin], ref["dx"]).max() < TOL
+    if second:
+        scale = {"d2v": ref["dv"] ** 2 + np.abs(ref["d2v"]), "d2x": ref["dx"] ** 2 + np.abs(ref["d2x"]),
+                 "dvx": np.abs(ref["dv"] * ref["dx"]) + np.abs(ref["dvx"])}
+        for k in ("d2v", "dvx", "d2x"):
+            g = _np(out[k])[fin]
+            nz = scale[k] > 0
+            assert (np.abs(g[nz] - ref[k][nz]) / scale[k][nz]).max() < TOL, k
+
+
 def test_mlp_path_full_size_sampled(net):
     """The bench's launch: 16,777,216 hard-band pairs, fast path at 32 bins, sampled check."""
     n = 16_777_216
