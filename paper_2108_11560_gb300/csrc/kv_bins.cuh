@@ -71,15 +71,27 @@ __device__ __forceinline__ T lane_sum(T a)
 
 struct BinsD {
     double v, x, t0, h, tp, s0, Lu;  // s0 = t0 - t_p, Lu = log1p(e^{-2 v t_p})
-    double e2u;                      // e^{-2 v t_p} (second derivatives only)
+    double e2u;                      // e^{-2 v t_p}
     double ep, em;                   // e^{t_p}, e^{-t_p}
+    double c1;                       // v - x sinh t_p
+    double xch, xsh;                 // x cosh t_p, x sinh t_p
     int n;
 };
 
-// FP64 bins.  Per bin five transcendentals: e^{-2vt}, log1p of it, sinh((t + t_p)/2),
-// expm1(s/2) and the weight's exp.  x (cosh t - cosh t_p) = 2 x sinh((t + t_p)/2) sinh(s/2) with
-// sinh(s/2) = (E - 1)(1 + 1/E)/2 from E - 1 = expm1(s/2) (no cancellation at small s), and
-// cosh t = (e^{t_p} E^2 + e^{-t_p} E^-2)/2, a sum of positive terms.
+// e^{+-s} and e^{-2vt} advance by one multiplication per bin and are recomputed exactly every
+// this many steps, so their relative error stays below this many ulps.
+constexpr int kRefreshF64 = 32;
+
+// FP64 bins, one transcendental per bin (the weight's exp).  With s = t - t_p and u = v t_p,
+//   g(t) - g(t_p) = c1 s + [log1p(e^{-2vt}) - log1p(e^{-2u})] + N(s),
+//   c1 = v - x sinh t_p,  N(s) = -(x e^{t_p}/2) phi(s) - (x e^{-t_p}/2) phi(-s),  phi(s) = e^s - 1 - s,
+// and the weight is taken as e^{g(t) - g(t_p)} = (1 + e^{-2vt}) / (1 + e^{-2u}) exp(c1 s + N(s)),
+// so no log1p is evaluated; the tanh integrand is w tanh(vt) = (1 - e^{-2vt}) / (1 + e^{-2u})
+// exp(...), with 1 - e^{-2vt} = -expm1(-2vt) below vt = 1/2 (no cancellation) and no division.
+// phi(+-s) = z (E(z) +- s O(z)), z = s^2, from the even/odd Taylor series for |s| <= 1 (terms to
+// s^20 and s^19: relative error below 1e-17), so N = -z (x cosh t_p E + x sinh t_p s O); beyond,
+// from e^{+-s}, where e^s - 1 - s loses at most a factor e/phi(1) < 4 of e^s's accuracy.  The
+// cosh t integrand is (e^{t_p} e^s + e^{-t_p} e^{-s})/2, a sum of positive terms.
 template <int L, bool DERIV>
 __device__ __forceinline__ void sums_f64(const BinsD& b, int lane, double& S0, double& S1, double& S2)
 {
@@ -87,23 +99,60 @@ __device__ __forceinline__ void sums_f64(const BinsD& b, int lane, double& S0, d
     k0.init();
     k1.init();
     k2.init();
+    const double kc = 1.0 / (1.0 + b.e2u);  // e^{-log1p(e^{-2u})}
+    const double ap = 0.5 * b.x * b.ep, am = 0.5 * b.x * b.em;
+    const double step = L * b.h;
+    const double qs = exp(step), qsi = exp(-step), q2 = exp(-2.0 * b.v * step);
+    double es = 1.0, esi = 1.0, e2 = 1.0;
+    int since = kRefreshF64;
     for (int m = lane; m <= b.n; m += L) {
-        double t = b.t0 + m * b.h;
-        double s = b.s0 + m * b.h;
-        double e2 = exp(-2.0 * b.v * t);
-        double dlc = b.v * s + (log1p(e2) - b.Lu);  // log cosh(vt) - log cosh(u)
-        const double em1 = expm1(0.5 * s);
-        const double ri = 1.0 / (1.0 + em1);                           // e^{-s/2}
-        const double sh = 0.5 * em1 * (1.0 + ri);                      // sinh(s/2)
-        double dxc = 2.0 * b.x * sinh(0.5 * (t + b.tp)) * sh;          // x (cosh t - cosh t_p)
-        double c = (m == 0 || m == b.n) ? 0.5 : 1.0;
-        double w = c * exp(dlc - dxc);
+        const double s = fma((double)m, b.h, b.s0);
+        const double t = b.tp + s;
+        if (since == kRefreshF64) {
+            es = exp(s);
+            esi = 1.0 / es;
+            e2 = exp(-2.0 * b.v * t);
+            since = 0;
+        }
+        const double z = s * s;
+        double E = 1.0 / 2432902008176640000.0;  // 1/20!
+        E = fma(E, z, 1.0 / 6402373705728000.0);  // 1/18!
+        E = fma(E, z, 1.0 / 20922789888000.0);    // 1/16!
+        E = fma(E, z, 1.0 / 87178291200.0);       // 1/14!
+        E = fma(E, z, 1.0 / 479001600.0);         // 1/12!
+        E = fma(E, z, 1.0 / 3628800.0);           // 1/10!
+        E = fma(E, z, 1.0 / 40320.0);             // 1/8!
+        E = fma(E, z, 1.0 / 720.0);               // 1/6!
+        E = fma(E, z, 1.0 / 24.0);                // 1/4!
+        E = fma(E, z, 0.5);                       // 1/2!
+        double O = 1.0 / 121645100408832000.0;   // 1/19!
+        O = fma(O, z, 1.0 / 355687428096000.0);   // 1/17!
+        O = fma(O, z, 1.0 / 1307674368000.0);     // 1/15!
+        O = fma(O, z, 1.0 / 6227020800.0);        // 1/13!
+        O = fma(O, z, 1.0 / 39916800.0);          // 1/11!
+        O = fma(O, z, 1.0 / 362880.0);            // 1/9!
+        O = fma(O, z, 1.0 / 5040.0);              // 1/7!
+        O = fma(O, z, 1.0 / 120.0);               // 1/5!
+        O = fma(O, z, 1.0 / 6.0);                 // 1/3!
+        const double n_small = -z * fma(b.xch, E, b.xsh * (s * O));
+        const double n_large = fma(b.xsh, s, b.xch) - fma(ap, es, am * esi);
+        const double N = fabs(s) <= 1.0 ? n_small : n_large;
+        const double c = (m == 0 || m == b.n) ? 0.5 : 1.0;
+        const double wp = c * kc * exp(fma(b.c1, s, N));
+        const double w = wp * (1.0 + e2);
         k0.add(w);
         if (DERIV) {
-            k1.add(w * t * ((1.0 - e2) / (1.0 + e2)));
-            const double eh = 1.0 + em1;                               // e^{s/2}
-            k2.add(w * (0.5 * fma(b.ep, eh * eh, b.em * (ri * ri)))); // cosh t
+            const double vt = b.v * t;
+            double q = 1.0 - e2;  // (1 + e^{-2vt}) tanh(vt)
+            if (vt < 0.5) q = -expm1(-2.0 * vt);
+            k1.add(wp * (t * q));
+            const double ch = 0.5 * fma(b.ep, es, b.em * esi);  // cosh t
+            k2.add(w > 0.0 ? w * ch : 0.0);
         }
+        es *= qs;
+        esi *= qsi;
+        e2 *= q2;
+        ++since;
     }
     S0 = lane_sum<double, L>(k0.value());
     S1 = DERIV ? lane_sum<double, L>(k1.value()) : 0.0;

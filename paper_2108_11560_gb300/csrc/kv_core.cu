@@ -222,12 +222,16 @@ __global__ void __launch_bounds__(kBlock) kv_f64_kernel(KParams p)
         b.h = (br.t1 - br.t0) / p.bins;
         b.tp = br.tp;
         b.s0 = br.t0 - br.tp;
-        b.Lu = log1p(exp(-2.0 * va * br.tp));
+        b.e2u = exp(-2.0 * va * br.tp);
+        b.Lu = log1p(b.e2u);
         b.ep = exp(br.tp);
         b.em = 1.0 / b.ep;
+        const double shp = sinh(br.tp);
+        b.c1 = fma(-xa, shp, va);
+        b.xch = xa * cosh(br.tp);
+        b.xsh = xa * shp;
         b.n = p.bins;
         if constexpr (D2) {
-            b.e2u = exp(-2.0 * va * br.tp);
             const Sums2<double> m = sums2_f64<L>(b, lane);
             if (active) {
                 double d2v, dvx, d2x;
