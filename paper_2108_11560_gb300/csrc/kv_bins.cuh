@@ -88,10 +88,14 @@ constexpr int kRefreshF64 = 32;
 // and the weight is taken as e^{g(t) - g(t_p)} = (1 + e^{-2vt}) / (1 + e^{-2u}) exp(c1 s + N(s)),
 // so no log1p is evaluated; the tanh integrand is w tanh(vt) = (1 - e^{-2vt}) / (1 + e^{-2u})
 // exp(...), with 1 - e^{-2vt} = -expm1(-2vt) below vt = 1/2 (no cancellation) and no division.
-// phi(+-s) = z (E(z) +- s O(z)), z = s^2, from the even/odd Taylor series for |s| <= 1 (terms to
-// s^20 and s^19: relative error below 1e-17), so N = -z (x cosh t_p E + x sinh t_p s O); beyond,
-// from e^{+-s}, where e^s - 1 - s loses at most a factor e/phi(1) < 4 of e^s's accuracy.  The
-// cosh t integrand is (e^{t_p} e^s + e^{-t_p} e^{-s})/2, a sum of positive terms.
+// phi(+-s) = z (E(z) +- s O(z)), z = s^2, for |s| <= 1 with E = (cosh s - 1)/z and
+// O = (sinh s / s - 1)/z as degree-6 minimax polynomials on z in [0, 1] (minimax_coeffs.py:
+// absolute errors 5.9e-18 and 3.5e-19, below double rounding), so
+// N = -z (x cosh t_p E + x sinh t_p s O); beyond, from e^{+-s}, where e^s - 1 - s loses at most a
+// factor e/phi(1) < 4 of e^s's accuracy.  The cosh t integrand is (e^{t_p} e^s + e^{-t_p} e^{-s})/2,
+// a sum of positive terms.  The three sums are plain within each block of kRefreshF64 steps
+// (relative error below 31 ulps: all terms are positive) and compensated (Kahan) across blocks,
+// so the summation error does not grow with the bin count.
 template <int L, bool DERIV>
 __device__ __forceinline__ void sums_f64(const BinsD& b, int lane, double& S0, double& S1, double& S2)
 {
@@ -99,6 +103,7 @@ __device__ __forceinline__ void sums_f64(const BinsD& b, int lane, double& S0, d
     k0.init();
     k1.init();
     k2.init();
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0;  // this block's plain sums
     const double kc = 1.0 / (1.0 + b.e2u);  // e^{-log1p(e^{-2u})}
     const double ap = 0.5 * b.x * b.ep, am = 0.5 * b.x * b.em;
     const double step = L * b.h;
@@ -113,47 +118,51 @@ __device__ __forceinline__ void sums_f64(const BinsD& b, int lane, double& S0, d
             esi = 1.0 / es;
             e2 = exp(-2.0 * b.v * t);
             since = 0;
+            k0.add(p0);
+            k1.add(p1);
+            k2.add(p2);
+            p0 = p1 = p2 = 0.0;
         }
         const double z = s * s;
-        double E = 1.0 / 2432902008176640000.0;  // 1/20!
-        E = fma(E, z, 1.0 / 6402373705728000.0);  // 1/18!
-        E = fma(E, z, 1.0 / 20922789888000.0);    // 1/16!
-        E = fma(E, z, 1.0 / 87178291200.0);       // 1/14!
-        E = fma(E, z, 1.0 / 479001600.0);         // 1/12!
-        E = fma(E, z, 1.0 / 3628800.0);           // 1/10!
-        E = fma(E, z, 1.0 / 40320.0);             // 1/8!
-        E = fma(E, z, 1.0 / 720.0);               // 1/6!
-        E = fma(E, z, 1.0 / 24.0);                // 1/4!
-        E = fma(E, z, 0.5);                       // 1/2!
-        double O = 1.0 / 121645100408832000.0;   // 1/19!
-        O = fma(O, z, 1.0 / 355687428096000.0);   // 1/17!
-        O = fma(O, z, 1.0 / 1307674368000.0);     // 1/15!
-        O = fma(O, z, 1.0 / 6227020800.0);        // 1/13!
-        O = fma(O, z, 1.0 / 39916800.0);          // 1/11!
-        O = fma(O, z, 1.0 / 362880.0);            // 1/9!
-        O = fma(O, z, 1.0 / 5040.0);              // 1/7!
-        O = fma(O, z, 1.0 / 120.0);               // 1/5!
-        O = fma(O, z, 1.0 / 6.0);                 // 1/3!
+        double E = 1.1639213882575488e-11;  // degree-6 minimax polynomials on z in [0, 1]
+        E = fma(E, z, 2.087443498312207e-9);
+        E = fma(E, z, 2.7557335075601938e-7);
+        E = fma(E, z, 2.4801587246062242e-5);
+        E = fma(E, z, 1.3888888888981485e-3);
+        E = fma(E, z, 4.1666666666666088e-2);
+        E = fma(E, z, 0.5);
+        double O = 7.7461889806431037e-13;
+        O = fma(O, z, 1.6057679312178728e-10);
+        O = fma(O, z, 2.5052117699413503e-8);
+        O = fma(O, z, 2.755731919136364e-6);
+        O = fma(O, z, 1.9841269841324241e-4);
+        O = fma(O, z, 8.3333333333332993e-3);
+        O = fma(O, z, 0.16666666666666667);
         const double n_small = -z * fma(b.xch, E, b.xsh * (s * O));
         const double n_large = fma(b.xsh, s, b.xch) - fma(ap, es, am * esi);
         const double N = fabs(s) <= 1.0 ? n_small : n_large;
         const double c = (m == 0 || m == b.n) ? 0.5 : 1.0;
         const double wp = c * kc * exp(fma(b.c1, s, N));
-        const double w = wp * (1.0 + e2);
-        k0.add(w);
+        // rounded products and sums (never contracted into an FMA), so that log K comes out the
+        // same bits with and without the derivative sums
+        const double w = __dmul_rn(wp, 1.0 + e2);
+        p0 = __dadd_rn(p0, w);
         if (DERIV) {
             const double vt = b.v * t;
             double q = 1.0 - e2;  // (1 + e^{-2vt}) tanh(vt)
             if (vt < 0.5) q = -expm1(-2.0 * vt);
-            k1.add(wp * (t * q));
+            p1 = fma(wp, t * q, p1);
             const double ch = 0.5 * fma(b.ep, es, b.em * esi);  // cosh t
-            k2.add(w > 0.0 ? w * ch : 0.0);
+            p2 += w > 0.0 ? w * ch : 0.0;
         }
         es *= qs;
         esi *= qsi;
         e2 *= q2;
         ++since;
     }
+    k0.add(p0);
+    k1.add(p1);
+    k2.add(p2);
     S0 = lane_sum<double, L>(k0.value());
     S1 = DERIV ? lane_sum<double, L>(k1.value()) : 0.0;
     S2 = DERIV ? lane_sum<double, L>(k2.value()) : 0.0;

@@ -6,6 +6,8 @@ interval, for
   O(z) = (sinh sqrt(z) / sqrt(z) - 1) / z     on z in [0, 1]         (degree 3)
   P(z) = (tanh(sqrt z) / sqrt z - 1) / z      on z in [0, 0.35^2]    (degree 3)
 
+and, for the FP64 bins, E and O on z in [0, 1] at degree 6.
+
 E and O are the even and odd parts of phi(s) = e^s - 1 - s = z (E(z) + s O(z)), z = s^2; P gives
 tanh(y) = y + y^3 P(y^2).  Not used at run time: the kernel holds the printed values.
 
@@ -68,6 +70,11 @@ def remez(f, a, b, deg, iters=30, grid=4000):
 
 
 if __name__ == "__main__":
+    # FP32 bins: degree 3
     for name, f, hi in (("E", _E, mp.mpf(1)), ("O", _O, mp.mpf(1)), ("P", _P, mp.mpf("0.35") ** 2)):
         c, e = remez(f, mp.mpf(0), hi, 3)
+        print(f"{name}: " + ", ".join(mp.nstr(cj, 17) for cj in c) + f"   max abs error {mp.nstr(e, 3)}")
+    # FP64 bins: degree 6 (17 significant digits round to the nearest double)
+    for name, f in (("E64", _E), ("O64", _O)):
+        c, e = remez(f, mp.mpf(0), mp.mpf(1), 6, grid=8000)
         print(f"{name}: " + ", ".join(mp.nstr(cj, 17) for cj in c) + f"   max abs error {mp.nstr(e, 3)}")
