@@ -8,10 +8,11 @@
 // The difference g(t_m) - g(t_p) is never formed by subtracting two large values.  With
 // s = t - t_p and u = v t_p (t, t_p >= 0):
 //   log cosh(vt) - log cosh(u) = v s + log1p(e^{-2vt}) - log1p(e^{-2u})
-//   x (cosh t - cosh t_p)      = 2 x sinh((t + t_p)/2) sinh(s/2)                    (FP64 bins)
-//                              = x sinh(t_p) s + (x e^{t_p}/2) phi(s) + (x e^{-t_p}/2) phi(-s)
-//                                with phi(s) = e^s - 1 - s >= 0                      (FP32 bins)
-// so that in FP32 every term is small where the weight is large and no two large terms cancel:
+//   x (cosh t - cosh t_p)      = x sinh(t_p) s + (x e^{t_p}/2) phi(s) + (x e^{-t_p}/2) phi(-s)
+//                                with phi(s) = e^s - 1 - s >= 0
+//                              ( = 2 x sinh((t + t_p)/2) sinh(s/2), used by the FP64 second-
+//                                derivative sums)
+// so that every term is small where the weight is large and no two large terms cancel:
 //   g(t) - g(t_p) = (v - x sinh t_p) s + [log1p(e^{-2vt}) - log1p(e^{-2u})]
 //                   - (x e^{t_p}/2) phi(s) - (x e^{-t_p}/2) phi(-s).
 // The per-pair constants (v - x sinh t_p, x e^{+-t_p}/2, log1p(e^{-2u}), g(t_p)) carry extra
