@@ -53,10 +53,10 @@ MIXED_LOG_EPS = -20.0
 FP32_OPS_PER_BIN = 35.92
 MUFU_OPS_PER_BIN = 4
 FP32_OPS_PER_PAIR = 505.1
-# DRAM bytes per pair of the fast-path kernel, from one ncu capture (50.39 MB read + 5.11 MB
+# DRAM bytes per pair of the fast-path kernel, from one ncu capture (50.39 MB read + 4.96 MB
 # written for 4,194,304 pairs; profiles/kv_mlp_tc_kernel_hard_band_4M.md), scaled to a launch.
 # Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES_PER_PAIR = (50.385664e6 + 5.10976e6) / 4194304
+TRAFFIC_BYTES_PER_PAIR = (50.386688e6 + 4.958464e6) / 4194304
 
 
 def _peaks():
