@@ -537,40 +537,72 @@ __device__ Sums2<double> sums2_f64(const BinsD& b, int lane)
     return lane_sums2<double, L>(k);
 }
 
+// expm1(y) for |y| < 1/2: y (1 + y/2 + ... + y^7/8!), relative error about 1e-8 before rounding.
+__device__ __forceinline__ float expm1_small(float y)
+{
+    float p = 1.0f / 40320.0f;
+    p = fmaf(p, y, 1.0f / 5040.0f);
+    p = fmaf(p, y, 1.0f / 720.0f);
+    p = fmaf(p, y, 1.0f / 120.0f);
+    p = fmaf(p, y, 1.0f / 24.0f);
+    p = fmaf(p, y, 1.0f / 6.0f);
+    p = fmaf(p, y, 0.5f);
+    return fmaf(y * y, p, y);
+}
+
+// Bins per block of the FP32 second-derivative sums: plain sums within a block, compensated
+// (Kahan) across blocks.
+constexpr int kBlockSums2 = 8;
+
+// The seven sums in FP32 with the fast path's weight split: w = c e^{-lu} (1 + e^{-2vt})
+// 2^{c1 s + N(s)} (no log1p), 1/(1 + e^{-2vt}) from the approximate reciprocal, e^{-2vt} - e^{-2u}
+// as e^{-2u} expm1(-2vs) from a short polynomial where |2vs| < 1/2.
 template <int L>
 __device__ Sums2<float> sums2_f32(const BinsF& b, int lane)
 {
     const BinsK kk = bins_k(b);
     KahanSum<float> k[7];
-    for (int j = 0; j < 7; ++j) k[j].init();
-    const float rope_u = 1.0f / (1.0f + b.e2u);
+    float q[7];
+    for (int j = 0; j < 7; ++j) {
+        k[j].init();
+        q[j] = 0.0f;
+    }
+    int in_block = 0;
     float mf = (float)lane;
     for (int m = lane; m <= b.n; m += L, mf += (float)L) {
         const float s = fmaf(mf, b.h, b.s0);
         float php, phm, es, ems;
         phi_pair(s, php, phm, es, ems);
-        const float vt = fmaf(b.v, s, b.u);
-        const float e2 = ex2_approx(-2.0f * LOG2E_F * vt);
+        const float ea = fmaf(kk.nv2, s, kk.nu2);
+        const float e2 = ex2_approx(ea);  // e^{-2vt}
         const float ope = 1.0f + e2;
-        const float dg = fmaf(kk.c1, s, lg2_approx(ope)) - fmaf(kk.ap, php, fmaf(kk.am, phm, kk.lu));
-        const float c = (m == 0 || m == b.n) ? 0.5f : 1.0f;
-        const float w = c * ex2_approx(dg);
-        const float rope = 1.0f / ope;
+        const float rope = rcp_approx(ope);
+        const float c = ((m == 0 || m == b.n) ? 0.5f : 1.0f) * kk.kc;
+        const float w = c * ope * ex2_approx(fmaf(kk.c1, s, -fmaf(kk.ap, php, kk.am * phm)));
+        const float vt = fmaf(b.v, s, b.u);
         const float th = vt < TANH_SERIES_MAX ? tanh_small(vt) : (1.0f - e2) * rope;
         const float t = b.tp + s;
         const float vs2 = -2.0f * b.v * s;
-        const float de = fabsf(vs2) < 0.5f ? b.e2u * expm1f(vs2) : e2 - b.e2u;  // e^{-2vt} - e^{-2u}
-        const float da = s * th - b.tp * 2.0f * de * rope * rope_u;
+        const float de = fabsf(vs2) < 0.5f ? b.e2u * expm1_small(vs2) : e2 - b.e2u;  // e^{-2vt} - e^{-2u}
+        const float da = s * th - b.tp * 2.0f * de * rope * kk.kc;
         const float dc = fmaf(b.shp, s, 0.5f * fmaf(b.ep, php, b.em * phm));
-        const float q = t * t * 4.0f * e2 * rope * rope;
-        k[0].add(w);
-        k[1].add(w * da);
-        k[2].add(w * da * da);
-        k[3].add(w * dc);
-        k[4].add(w * dc * dc);
-        k[5].add(w * da * dc);
-        k[6].add(w * q);
+        const float wda = w * da, wdc = w * dc;
+        q[0] += w;
+        q[1] += wda;
+        q[2] = fmaf(wda, da, q[2]);
+        q[3] += wdc;
+        q[4] = fmaf(wdc, dc, q[4]);
+        q[5] = fmaf(wda, dc, q[5]);
+        q[6] = fmaf(w * (t * t), 4.0f * e2 * rope * rope, q[6]);
+        if (++in_block == kBlockSums2) {
+            for (int j = 0; j < 7; ++j) {
+                k[j].add(q[j]);
+                q[j] = 0.0f;
+            }
+            in_block = 0;
+        }
     }
+    for (int j = 0; j < 7; ++j) k[j].add(q[j]);
     return lane_sums2<float, L>(k);
 }
 
