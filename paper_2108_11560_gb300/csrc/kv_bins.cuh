@@ -76,8 +76,30 @@ struct BinsD {
     double ep, em;                   // e^{t_p}, e^{-t_p}
     double c1;                       // v - x sinh t_p
     double xch, xsh;                 // x cosh t_p, x sinh t_p
+    double shp;                      // sinh t_p
     int n;
 };
+
+// E(z) = (cosh s - 1)/z and O(z) = (sinh s / s - 1)/z, z = s^2 <= 1, as degree-6 minimax
+// polynomials (minimax_coeffs.py: absolute errors 5.9e-18 and 3.5e-19, below double rounding);
+// phi(+-s) = e^{+-s} - 1 -+ s = z (E +- s O).
+__device__ __forceinline__ void phi_parts_f64(double z, double& E, double& O)
+{
+    E = 1.1639213882575488e-11;
+    E = fma(E, z, 2.087443498312207e-9);
+    E = fma(E, z, 2.7557335075601938e-7);
+    E = fma(E, z, 2.4801587246062242e-5);
+    E = fma(E, z, 1.3888888888981485e-3);
+    E = fma(E, z, 4.1666666666666088e-2);
+    E = fma(E, z, 0.5);
+    O = 7.7461889806431037e-13;
+    O = fma(O, z, 1.6057679312178728e-10);
+    O = fma(O, z, 2.5052117699413503e-8);
+    O = fma(O, z, 2.755731919136364e-6);
+    O = fma(O, z, 1.9841269841324241e-4);
+    O = fma(O, z, 8.3333333333332993e-3);
+    O = fma(O, z, 0.16666666666666667);
+}
 
 // e^{+-s} and e^{-2vt} advance by one multiplication per bin and are recomputed exactly every
 // this many steps, so their relative error stays below this many ulps.
@@ -125,20 +147,8 @@ __device__ __forceinline__ void sums_f64(const BinsD& b, int lane, double& S0, d
             p0 = p1 = p2 = 0.0;
         }
         const double z = s * s;
-        double E = 1.1639213882575488e-11;  // degree-6 minimax polynomials on z in [0, 1]
-        E = fma(E, z, 2.087443498312207e-9);
-        E = fma(E, z, 2.7557335075601938e-7);
-        E = fma(E, z, 2.4801587246062242e-5);
-        E = fma(E, z, 1.3888888888981485e-3);
-        E = fma(E, z, 4.1666666666666088e-2);
-        E = fma(E, z, 0.5);
-        double O = 7.7461889806431037e-13;
-        O = fma(O, z, 1.6057679312178728e-10);
-        O = fma(O, z, 2.5052117699413503e-8);
-        O = fma(O, z, 2.755731919136364e-6);
-        O = fma(O, z, 1.9841269841324241e-4);
-        O = fma(O, z, 8.3333333333332993e-3);
-        O = fma(O, z, 0.16666666666666667);
+        double E, O;
+        phi_parts_f64(z, E, O);
         const double n_small = -z * fma(b.xch, E, b.xsh * (s * O));
         const double n_large = fma(b.xsh, s, b.xch) - fma(ap, es, am * esi);
         const double N = fabs(s) <= 1.0 ? n_small : n_large;
@@ -506,34 +516,75 @@ __device__ __forceinline__ Sums2<T> lane_sums2(const KahanSum<T> (&k)[7])
     return m;
 }
 
+// The seven sums in FP64 with the first-derivative bins' scheme (sums_f64): the weight as
+// (1 + e^{-2vt})/(1 + e^{-2u}) exp(c1 s + N(s)), phi(+-s) from the minimax polynomials for |s| <= 1
+// and from e^{+-s} beyond, e^{+-s} and e^{-2vt} by recurrence with an exact refresh every
+// kRefreshF64 steps, sums plain within a block and compensated across blocks; dc = cosh t -
+// cosh t_p = sinh t_p s + (e^{t_p} phi(s) + e^{-t_p} phi(-s))/2 from the same phi values, and
+// e^{-2vt} - e^{-2u} = e^{-2u} expm1(-2vs) where |2vs| < 1/2.
 template <int L>
 __device__ Sums2<double> sums2_f64(const BinsD& b, int lane)
 {
     KahanSum<double> k[7];
-    for (int j = 0; j < 7; ++j) k[j].init();
-    const double ope_u = 1.0 + b.e2u;
-    for (int m = lane; m <= b.n; m += L) {
-        const double t = b.t0 + m * b.h;
-        const double s = b.s0 + m * b.h;
-        const double e2 = exp(-2.0 * b.v * t);
-        const double dlc = b.v * s + (log1p(e2) - b.Lu);
-        const double dc = 2.0 * sinh(0.5 * (t + b.tp)) * sinh(0.5 * s);  // cosh t - cosh t_p
-        const double c = (m == 0 || m == b.n) ? 0.5 : 1.0;
-        const double w = c * exp(dlc - b.x * dc);
-        const double ope = 1.0 + e2;
-        const double th = (1.0 - e2) / ope;
-        const double vs2 = -2.0 * b.v * s;
-        const double de = fabs(vs2) < 0.5 ? b.e2u * expm1(vs2) : e2 - b.e2u;  // e^{-2vt} - e^{-2u}
-        const double da = s * th - b.tp * 2.0 * de / (ope * ope_u);
-        const double q = t * t * 4.0 * e2 / (ope * ope);
-        k[0].add(w);
-        k[1].add(w * da);
-        k[2].add(w * da * da);
-        k[3].add(w * dc);
-        k[4].add(w * dc * dc);
-        k[5].add(w * da * dc);
-        k[6].add(w * q);
+    double q[7];
+    for (int j = 0; j < 7; ++j) {
+        k[j].init();
+        q[j] = 0.0;
     }
+    const double kc = 1.0 / (1.0 + b.e2u);
+    const double ap = 0.5 * b.x * b.ep, am = 0.5 * b.x * b.em;
+    const double step = L * b.h;
+    const double qs = exp(step), qsi = exp(-step), q2 = exp(-2.0 * b.v * step);
+    double es = 1.0, esi = 1.0, e2 = 1.0;
+    int since = kRefreshF64;
+    for (int m = lane; m <= b.n; m += L) {
+        const double s = fma((double)m, b.h, b.s0);
+        const double t = b.tp + s;
+        if (since == kRefreshF64) {
+            es = exp(s);
+            esi = 1.0 / es;
+            e2 = exp(-2.0 * b.v * t);
+            since = 0;
+            for (int j = 0; j < 7; ++j) {
+                k[j].add(q[j]);
+                q[j] = 0.0;
+            }
+        }
+        const double z = s * s;
+        double E, O;
+        phi_parts_f64(z, E, O);
+        const bool small = fabs(s) <= 1.0;
+        const double so = s * O;
+        const double php = small ? z * (E + so) : (es - 1.0) - s;   // phi(s)
+        const double phm = small ? z * (E - so) : (esi - 1.0) + s;  // phi(-s)
+        const double N = -fma(ap, php, am * phm);
+        const double dc = fma(b.shp, s, 0.5 * fma(b.ep, php, b.em * phm));
+        const double c = (m == 0 || m == b.n) ? 0.5 : 1.0;
+        const double ope = 1.0 + e2;
+        const double w = c * kc * ope * exp(fma(b.c1, s, N));
+        const double r = 1.0 / ope;
+        const double vt = b.v * t;
+        double qt = 1.0 - e2;  // (1 + e^{-2vt}) tanh(vt)
+        if (vt < 0.5) qt = -expm1(-2.0 * vt);
+        const double th = qt * r;
+        const double vs2 = -2.0 * b.v * s;
+        double de = e2 - b.e2u;  // e^{-2vt} - e^{-2u}
+        if (fabs(vs2) < 0.5) de = b.e2u * expm1(vs2);
+        const double da = s * th - b.tp * 2.0 * de * r * kc;
+        const double wda = w * da, wdc = w * dc;
+        q[0] += w;
+        q[1] += wda;
+        q[2] = fma(wda, da, q[2]);
+        q[3] += wdc;
+        q[4] = fma(wdc, dc, q[4]);
+        q[5] = fma(wda, dc, q[5]);
+        q[6] = fma(w * (t * t), 4.0 * e2 * r * r, q[6]);
+        es *= qs;
+        esi *= qsi;
+        e2 *= q2;
+        ++since;
+    }
+    for (int j = 0; j < 7; ++j) k[j].add(q[j]);
     return lane_sums2<double, L>(k);
 }
 

@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(kBlock) kv_f64_kernel(KParams p)
         b.c1 = fma(-xa, shp, va);
         b.xch = xa * cosh(br.tp);
         b.xsh = xa * shp;
+        b.shp = shp;
         b.n = p.bins;
         if constexpr (D2) {
             const Sums2<double> m = sums2_f64<L>(b, lane);
