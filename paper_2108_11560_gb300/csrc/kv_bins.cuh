@@ -588,72 +588,103 @@ __device__ Sums2<double> sums2_f64(const BinsD& b, int lane)
     return lane_sums2<double, L>(k);
 }
 
-// expm1(y) for |y| < 1/2: y (1 + y/2 + ... + y^7/8!), relative error about 1e-8 before rounding.
-__device__ __forceinline__ float expm1_small(float y)
+// expm1(y) for |y| < 1/2 (two values): y (1 + y/2 + ... + y^7/8!), relative error about 1e-8
+// before rounding.
+__device__ __forceinline__ float2 expm1_small2(float2 y)
 {
-    float p = 1.0f / 40320.0f;
-    p = fmaf(p, y, 1.0f / 5040.0f);
-    p = fmaf(p, y, 1.0f / 720.0f);
-    p = fmaf(p, y, 1.0f / 120.0f);
-    p = fmaf(p, y, 1.0f / 24.0f);
-    p = fmaf(p, y, 1.0f / 6.0f);
-    p = fmaf(p, y, 0.5f);
-    return fmaf(y * y, p, y);
+    float2 p = f2(1.0f / 40320.0f);
+    p = fma2(p, y, f2(1.0f / 5040.0f));
+    p = fma2(p, y, f2(1.0f / 720.0f));
+    p = fma2(p, y, f2(1.0f / 120.0f));
+    p = fma2(p, y, f2(1.0f / 24.0f));
+    p = fma2(p, y, f2(1.0f / 6.0f));
+    p = fma2(p, y, f2(0.5f));
+    return fma2(mul2(y, y), p, y);
 }
 
 // Bins per block of the FP32 second-derivative sums: plain sums within a block, compensated
 // (Kahan) across blocks.
 constexpr int kBlockSums2 = 8;
 
-// The seven sums in FP32 with the fast path's weight split: w = c e^{-lu} (1 + e^{-2vt})
-// 2^{c1 s + N(s)} (no log1p), 1/(1 + e^{-2vt}) from the approximate reciprocal, e^{-2vt} - e^{-2u}
-// as e^{-2u} expm1(-2vs) from a short polynomial where |2vs| < 1/2.
+// Two bins (the components of s; c = their weight factors c_m e^{-lu}) of the seven sums, in
+// paired FP32 instructions, added to acc: the fast path's weight split w = c (1 + e^{-2vt})
+// 2^{c1 s + N(s)} (no log1p), 1/(1 + e^{-2vt}) from the approximate reciprocal, tanh(vt) from its
+// polynomial below vt = 0.35, e^{-2vt} - e^{-2u} as e^{-2u} expm1(-2vs) from a polynomial where
+// |2vs| < 1/2, and dc = cosh t - cosh t_p = sinh t_p s + (e^{t_p} phi(s) + e^{-t_p} phi(-s))/2.
+__device__ __forceinline__ void sums2_bins2(const BinsF& b, const BinsK& kk, float2 s, float2 c,
+                                            float (&acc)[7])
+{
+    const float2 z = mul2(s, s);
+    float2 E, O;
+    KV_PHI_SERIES(mul2, fma2, f2, z, E, O)
+    const float2 so = mul2(s, O);
+    const float2 pp = mul2(z, add2(E, so)), pm = mul2(z, sub2(E, so));
+    const float2 el = mul2(s, f2(LOG2E_F));
+    const float2 es = make_float2(ex2_approx(el.x), ex2_approx(el.y));
+    const float2 ems = make_float2(rcp_approx(es.x), rcp_approx(es.y));
+    const float2 pl = sub2(add2(es, f2(-1.0f)), s), ml = add2(add2(ems, f2(-1.0f)), s);
+    const bool sx = fabsf(s.x) <= PHI_SERIES_MAX, sy = fabsf(s.y) <= PHI_SERIES_MAX;
+    const float2 php = make_float2(sx ? pp.x : pl.x, sy ? pp.y : pl.y);  // phi(s)
+    const float2 phm = make_float2(sx ? pm.x : ml.x, sy ? pm.y : ml.y);  // phi(-s)
+    const float2 ea = fma2(f2(kk.nv2), s, f2(kk.nu2));
+    const float2 e2 = make_float2(ex2_approx(ea.x), ex2_approx(ea.y));  // e^{-2vt}
+    const float2 ope = add2(f2(1.0f), e2);
+    const float2 rope = make_float2(rcp_approx(ope.x), rcp_approx(ope.y));
+    const float2 dg = fma2(f2(kk.c1), s, fma2(f2(kk.nap), php, mul2(f2(kk.nam), phm)));
+    const float2 w = mul2(mul2(c, ope), make_float2(ex2_approx(dg.x), ex2_approx(dg.y)));
+    const float2 vt = fma2(f2(b.v), s, f2(b.u));
+    const float2 ts = tanh_small2(vt), tl = mul2(sub2(f2(1.0f), e2), rope);
+    const float2 th = make_float2(vt.x < TANH_SERIES_MAX ? ts.x : tl.x, vt.y < TANH_SERIES_MAX ? ts.y : tl.y);
+    const float2 t = add2(f2(b.tp), s);
+    const float2 vs2 = mul2(f2(-2.0f * b.v), s);
+    const float2 des = mul2(f2(b.e2u), expm1_small2(vs2)), del = sub2(e2, f2(b.e2u));
+    const float2 de = make_float2(fabsf(vs2.x) < 0.5f ? des.x : del.x, fabsf(vs2.y) < 0.5f ? des.y : del.y);
+    const float2 da = fma2(s, th, mul2(f2(-2.0f * b.tp * kk.kc), mul2(de, rope)));
+    const float2 dc = fma2(f2(b.shp), s, mul2(f2(0.5f), fma2(f2(b.ep), php, mul2(f2(b.em), phm))));
+    const float2 wda = mul2(w, da), wdc = mul2(w, dc);
+    const float2 wq = mul2(mul2(w, mul2(t, t)), mul2(f2(4.0f), mul2(e2, mul2(rope, rope))));  // w t^2 sech^2(vt)
+    acc[0] += w.x + w.y;
+    acc[1] += wda.x + wda.y;
+    acc[2] = fmaf(wda.x, da.x, fmaf(wda.y, da.y, acc[2]));
+    acc[3] += wdc.x + wdc.y;
+    acc[4] = fmaf(wdc.x, dc.x, fmaf(wdc.y, dc.y, acc[4]));
+    acc[5] = fmaf(wda.x, dc.x, fmaf(wda.y, dc.y, acc[5]));
+    acc[6] += wq.x + wq.y;
+}
+
+// The seven sums over bins m = lane, lane + L, ... <= n, two bins per instruction (a last odd
+// bin runs as a pair whose second weight is 0).
 template <int L>
 __device__ Sums2<float> sums2_f32(const BinsF& b, int lane)
 {
     const BinsK kk = bins_k(b);
     KahanSum<float> k[7];
-    float q[7];
+    float acc[7];
     for (int j = 0; j < 7; ++j) {
         k[j].init();
-        q[j] = 0.0f;
+        acc[j] = 0.0f;
     }
     int in_block = 0;
+    int m = lane;
     float mf = (float)lane;
-    for (int m = lane; m <= b.n; m += L, mf += (float)L) {
-        const float s = fmaf(mf, b.h, b.s0);
-        float php, phm, es, ems;
-        phi_pair(s, php, phm, es, ems);
-        const float ea = fmaf(kk.nv2, s, kk.nu2);
-        const float e2 = ex2_approx(ea);  // e^{-2vt}
-        const float ope = 1.0f + e2;
-        const float rope = rcp_approx(ope);
-        const float c = ((m == 0 || m == b.n) ? 0.5f : 1.0f) * kk.kc;
-        const float w = c * ope * ex2_approx(fmaf(kk.c1, s, -fmaf(kk.ap, php, kk.am * phm)));
-        const float vt = fmaf(b.v, s, b.u);
-        const float th = vt < TANH_SERIES_MAX ? tanh_small(vt) : (1.0f - e2) * rope;
-        const float t = b.tp + s;
-        const float vs2 = -2.0f * b.v * s;
-        const float de = fabsf(vs2) < 0.5f ? b.e2u * expm1_small(vs2) : e2 - b.e2u;  // e^{-2vt} - e^{-2u}
-        const float da = s * th - b.tp * 2.0f * de * rope * kk.kc;
-        const float dc = fmaf(b.shp, s, 0.5f * fmaf(b.ep, php, b.em * phm));
-        const float wda = w * da, wdc = w * dc;
-        q[0] += w;
-        q[1] += wda;
-        q[2] = fmaf(wda, da, q[2]);
-        q[3] += wdc;
-        q[4] = fmaf(wdc, dc, q[4]);
-        q[5] = fmaf(wda, dc, q[5]);
-        q[6] = fmaf(w * (t * t), 4.0f * e2 * rope * rope, q[6]);
-        if (++in_block == kBlockSums2) {
+    for (; m + L <= b.n; m += 2 * L, mf += (float)(2 * L)) {
+        const float2 s = fma2(make_float2(mf, mf + (float)L), f2(b.h), f2(b.s0));
+        const float2 c = make_float2(m == 0 ? 0.5f * kk.kc : kk.kc, m + L == b.n ? 0.5f * kk.kc : kk.kc);
+        sums2_bins2(b, kk, s, c, acc);
+        in_block += 2;
+        if (in_block == kBlockSums2) {
             for (int j = 0; j < 7; ++j) {
-                k[j].add(q[j]);
-                q[j] = 0.0f;
+                k[j].add(acc[j]);
+                acc[j] = 0.0f;
             }
             in_block = 0;
         }
     }
-    for (int j = 0; j < 7; ++j) k[j].add(q[j]);
+    if (m <= b.n) {
+        const float s = fmaf(mf, b.h, b.s0);
+        sums2_bins2(b, kk, f2(s), make_float2((m == 0 || m == b.n) ? 0.5f * kk.kc : kk.kc, 0.0f), acc);
+    }
+    for (int j = 0; j < 7; ++j) k[j].add(acc[j]);
     return lane_sums2<float, L>(k);
 }
 

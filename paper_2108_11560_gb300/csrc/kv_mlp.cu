@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(kMlpBlock) kv_plain_f32_kernel(MlpPathParams p
 // than the 128 FMAs it saves.)  A wait that does not finish within its limit sends the CTA's
 // remaining pairs to the fallback list (correct, slower) instead of hanging.
 template <bool DERIV, bool D2 = false>
-__global__ void __launch_bounds__(kMlpBlock, 8) kv_mlp_tc_kernel(MlpPathParams p)
+__global__ void __launch_bounds__(kMlpBlock, D2 ? 6 : 8) kv_mlp_tc_kernel(MlpPathParams p)
 {
     __shared__ __align__(1024) TcSmem sm;
     const int t = threadIdx.x;
