@@ -32,15 +32,30 @@ struct PairD {
     double log_eps;  // log of the range's eps
 };
 
+// 1/(1 + e2) and 1/et from one division: q = 1/((1 + e2) et), then et q and (1 + e2) q (two
+// divisions where the product overflows, which only a capped doubling search far out reaches).
+__device__ __forceinline__ void two_reciprocals(double ope, double et, double& r, double& eti)
+{
+    const double d = ope * et;
+    if (d < INFINITY) {
+        const double q = 1.0 / d;
+        r = et * q;
+        eti = ope * q;
+    } else {
+        r = 1.0 / ope;
+        eti = 1.0 / et;
+    }
+}
+
 // g'(t) and g''(t) at t >= 0 (Sec. 2.1), sharing e^{-2vt} and e^t.
 __device__ __forceinline__ void eval_g1_g2(const PairD& p, double t, double& g1, double& g2)
 {
     double e2 = exp(-2.0 * p.v * t);
-    double r = 1.0 / (1.0 + e2);
+    double et = exp(t);
+    double r, eti;
+    two_reciprocals(1.0 + e2, et, r, eti);
     double th = (1.0 - e2) * r;      // tanh(vt)
     double sech2 = 4.0 * e2 * r * r; // sech^2(vt)
-    double et = exp(t);
-    double eti = 1.0 / et;
     g1 = p.v * th - p.x * 0.5 * (et - eti);
     g2 = p.v * p.v * sech2 - p.x * 0.5 * (et + eti);
 }
@@ -50,9 +65,10 @@ __device__ __forceinline__ void eval_h_h1(const PairD& p, double t, double& h, d
 {
     double a = p.v * t;
     double e2 = exp(-2.0 * a);
-    double th = (1.0 - e2) / (1.0 + e2);
     double et = exp(t);
-    double eti = 1.0 / et;
+    double r, eti;
+    two_reciprocals(1.0 + e2, et, r, eti);
+    double th = (1.0 - e2) * r;
     double g = a + log1p(e2) - LN2_D - p.x * 0.5 * (et + eti);
     h = g - p.G - p.log_eps;
     h1 = p.v * th - p.x * 0.5 * (et - eti);
