@@ -8,7 +8,7 @@ and the two share no code.
   Sec. 4.1 derivatives) in FP64 (``precision="double"``) or, with the same steps, in
   ``long double`` (``precision="long"``).
 * :func:`dense` -- the integral of Eq. (1)-(2) by adaptive Gauss-Legendre quadrature in
-  ``long double`` (the truth the method is judged against).
+  ``long double`` (the truth the method is measured against).
 * :mod:`oracle.mlp` -- the learned bracket's MLP forward/backward/Adam in float64 numpy.
 
 The C source is compiled on first use (or by :func:`build`) with gcc into ``oracle/_build``.

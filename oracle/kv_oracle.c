@@ -24,7 +24,7 @@
  *
  *   O2  (long double build only) The integral of Eq. (1)-(2) by dense adaptive Gauss-Legendre
  *       quadrature on a widened range found by a plain scan, independent of Algorithms 1-3.
- *       This is the truth that the method itself is judged against.
+ *       This is the truth that the method itself is measured against.
  *
  * Readings of passages that are garbled or silent (each also listed in the design notes):
  *   R1 FindZero's first argument is the end where the function is negative, the second the end
