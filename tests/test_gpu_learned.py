@@ -279,6 +279,25 @@ def test_tensor_core_wait_running_out_falls_back(net, second):
             assert (np.abs(g[nz] - ref[k][nz]) / scale[k][nz]).max() < TOL, k
 
 
+@pytest.mark.parametrize("n", [0, 1, 127, 129, 1_000_003])
+def test_mlp_path_ragged_sizes(net, n):
+    """Tiles of 128 pairs per CTA and a persistent grid: a size below one tile, around one tile,
+    and a large size with a ragged last tile, against the oracle's method (sampled)."""
+    v, x = W.hard_band(max(n, 1), seed=317)
+    (vf, v64), (xf, x64) = W.to_f32(v[:n], x[:n])
+    out = kv.kv_fwd_bwd_ex(_t(vf, torch.float32), _t(xf, torch.float32), bins=32, bracket="mlp", mlp=net)
+    if n == 0:
+        assert out["logk"].numel() == 0
+        return
+    idx = np.unique(np.concatenate([np.arange(min(n, 256)), np.arange(max(n - 256, 0), n),
+                                    np.random.default_rng(318).choice(n, min(n, 2000), replace=False)]))
+    ref = oracle.o1(v64[idx], x64[idx], bins=32, log_eps=LOG_EPS, precision="long")
+    assert rel_logk(_np(out["logk"])[idx], ref["logk"]).max() < TOL
+    z = v64[idx] == 0
+    assert rel(_np(out["dv"])[idx][~z], ref["dv"][~z]).max() < TOL
+    assert rel(_np(out["dx"])[idx], ref["dx"]).max() < TOL
+
+
 def test_mlp_path_full_size_sampled(net):
     """The bench's launch: 16,777,216 hard-band pairs, fast path at 32 bins, sampled check."""
     n = 16_777_216

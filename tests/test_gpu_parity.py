@@ -14,6 +14,7 @@ if not torch.cuda.is_available():
 
 import oracle
 from conftest import rel, rel_logk
+from paper_2108_11560_gb300 import _native as N
 from paper_2108_11560_gb300 import kv, learned
 from paper_2108_11560_gb300 import workloads as W
 
@@ -112,6 +113,30 @@ def test_ragged_sizes(n):
     ref = oracle.o1(v, x, bins=64, precision="long")
     assert rel_logk(_np(lk), ref["logk"]).max() < TOL_F64
     assert rel(_np(dx), ref["dx"]).max() < TOL_F64
+
+
+@pytest.mark.parametrize("bracket", ["plain64", "plain", "f32", "mlp"])
+def test_max_bins_every_path(bracket):
+    """The largest bin count the boundary accepts (KV_MAX_BINS) on every path: the FP64 bins'
+    recurrences (refreshed every 32 steps) and block sums, and the FP32 bins' block-compensated
+    sums, keep their accuracy over 4097 bins."""
+    v, x = W.full_domain(256, seed=215)
+    bins = N.KV_MAX_BINS
+    if bracket == "plain64":
+        lk, dv, dx = (_np(t) for t in kv.kv_fwd_bwd(_t(v), _t(x), bins=bins))
+        ref = oracle.o1(v, x, bins=bins, precision="long")
+        tol, v64 = TOL_F64, v
+    else:
+        (vf, v64), (xf, x64) = W.to_f32(v, x)
+        net = learned.default_network(DEV) if bracket == "mlp" else None
+        out = kv.kv_fwd_bwd_ex(_t(vf, torch.float32), _t(xf, torch.float32), bins=bins, bracket=bracket,
+                               mlp=net)
+        lk, dv, dx = (_np(out[k]) for k in ("logk", "dv", "dx"))
+        ref = oracle.o1(v64, x64, bins=bins, log_eps=MIXED_LOG_EPS, precision="long")
+        tol = TOL_MIXED
+    assert rel_logk(lk, ref["logk"]).max() < tol
+    assert _deriv_ok(dv, ref["dv"], v64, tol) < tol
+    assert rel(dx, ref["dx"]).max() < tol
 
 
 def test_edge_cases_both_paths():
