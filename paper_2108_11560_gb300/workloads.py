@@ -110,10 +110,12 @@ def paper_scaling(n: int, seed: int = 8):
 
 
 def paper_accuracy_grid(step: int = 1):
-    """The accuracy-map grid of Sec. 3.1: v = 10^{i/40} - 1, i = 0..80 and x = 10^{i/40},
-    i = 0..124 (every ``step``-th point on each axis).  Returns flattened (v, x)."""
+    """The accuracy-map grid of Sec. 3 over the range it states, v in [0, 99] and
+    x in [10^-1, 10^2.1]: v = 10^{i/40} - 1, i = 0..80 and x = 10^{(i - 40)/40}, i = 0..124 (125
+    points a fortieth of a decade apart; the exponent i/40 alone would start the axis at 1), every
+    ``step``-th point on each axis.  Returns flattened (v, x)."""
     v = 10.0 ** (np.arange(0, 81, step) / 40.0) - 1.0
-    x = 10.0 ** (np.arange(0, 125, step) / 40.0)
+    x = 10.0 ** ((np.arange(0, 125, step) - 40) / 40.0)
     vv, xx = np.meshgrid(v, x, indexing="ij")
     return vv.ravel(), xx.ravel()
 
