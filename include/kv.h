@@ -12,8 +12,7 @@
  * Conventions for every entry point below
  *   - Arrays are structure-of-arrays, n contiguous elements each, caller-owned DEVICE memory
  *     (except kv_fwd_bwd_host and kv_fwd_bwd_host_ex, which take host memory).  The library
- *     never keeps a pointer
- *     after the call's work on `stream` has finished.
+ *     never keeps a pointer after the call's work on `stream` has finished.
  *   - Element type is set by `dtype`: KV_F64 -> double for inputs and outputs;
  *     KV_MIXED -> float for inputs and outputs.  Pointers must be aligned to the element size.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls are
