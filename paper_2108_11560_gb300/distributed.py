@@ -1,10 +1,11 @@
 """Host-side helpers for one process per GPU.
 
 The pairs (v, x) are independent, so the path shards without any exchange: each rank takes a
-contiguous share of the arrays and computes it alone.  The only collectives are scalar ones
-outside the data path: the sum of a sharded log-likelihood sum_i log K(v_i, x_i) and the
-maximum of per-rank timings.  These helpers work with any torch.distributed backend (NCCL on
-GPUs, gloo in the CPU tests).
+contiguous share of the arrays and computes it alone.  The only collectives are outside the data
+path: the sum of a sharded log-likelihood sum_i log K(v_i, x_i), the maximum of per-rank timings,
+and, for training the learned bracket data-parallel, one all-reduce of the network's gradient per
+step.  These helpers work with any torch.distributed backend (NCCL on GPUs, gloo in the CPU
+tests).
 """
 from __future__ import annotations
 
@@ -45,3 +46,28 @@ def sharded_loglik(v, x, rank: int, world: int, local_sum, device=None) -> float
     `local_sum` (on a GPU: kv.kv_sum of kv.kv_log) and the partial sums meet in one all-reduce."""
     lo, hi = shard_bounds(len(v), rank, world)
     return all_reduce_scalar(float(local_sum(v[lo:hi], x[lo:hi])), "sum", device)
+
+
+def all_reduce_gradient(loss: float, grad, count: int, device=None):
+    """Mean loss and gradient over a batch split across ranks: each rank passes the mean loss and
+    gradient over its `count` samples (on a GPU: kv_mlp_loss_grad on its share), and the
+    count-weighted sums meet in one all-reduce, so every rank gets the full batch's mean (the
+    data-parallel step of training the learned bracket; ~4.5k parameters).  Without a process
+    group the arguments come back unchanged.  Returns (loss, grad) with grad shaped like the
+    input, in float64."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(loss), np.asarray(grad, dtype=np.float64)
+    g = torch.as_tensor(np.asarray(grad, dtype=np.float64)).reshape(-1)
+    buf = torch.cat([g * float(count), torch.tensor([float(loss) * count, float(count)], dtype=torch.float64)])
+    if device is not None:
+        buf = buf.to(device)
+    dist.all_reduce(buf)
+    buf = buf.cpu()
+    total = float(buf[-1])
+    if total <= 0:
+        raise ValueError("no samples on any rank")
+    return float(buf[-2]) / total, (buf[:-2] / total).numpy().reshape(np.shape(grad))

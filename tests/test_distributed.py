@@ -1,6 +1,8 @@
-"""Multi-process host logic on CPU (gloo, world size 2): shards cover the pairs exactly once and
-the sharded log-likelihood equals the serial one.  The per-rank partial sums come from the CPU
-oracle here (the GPU path computes them with kv_sum on each rank's device)."""
+"""Multi-process host logic on CPU (gloo, world size 2): shards cover the pairs exactly once, the
+sharded log-likelihood equals the serial one, and the data-parallel gradient of the learned
+bracket equals the full batch's.  The per-rank partial sums and gradients come from the CPU
+oracles here (the GPU path computes them with kv_sum and kv_mlp_loss_grad on each rank's
+device)."""
 import os
 import socket
 
@@ -79,3 +81,58 @@ def test_sharded_loglik_gloo_world_2():
         total, tmax = out[r]
         assert abs(total - serial) <= 1e-9 * abs(serial)
         assert tmax == float(world)
+
+
+def _grad_batch():
+    from oracle import mlp as omlp
+    from paper_2108_11560_gb300 import workloads as W
+
+    rng = np.random.default_rng(17)
+    p = rng.standard_normal(omlp.NPARAMS) * 0.1
+    v, x = W.learned_bracket(301, seed=18)
+    tp = omlp.peak(v, x)
+    t0 = np.maximum(tp - rng.uniform(0.01, 2.0, v.size), 0.0)
+    t1 = tp + rng.uniform(0.01, 4.0, v.size)
+    return p, v, x, t0, tp, t1
+
+
+def _grad_worker(rank, world, port, out):
+    import torch.distributed as dist
+
+    from oracle import mlp as omlp
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        p, v, x, t0, tp, t1 = _grad_batch()
+        lo, hi = D.shard_bounds(v.size, rank, world)  # unequal shares: 151 and 150 samples
+        loss, g = omlp.loss_grad(p, v[lo:hi], x[lo:hi], t0[lo:hi], tp[lo:hi], t1[lo:hi])
+        out[rank] = D.all_reduce_gradient(loss, g, hi - lo)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_data_parallel_gradient_gloo_world_2():
+    from oracle import mlp as omlp
+
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    manager = ctx.Manager()
+    out = manager.dict()
+    procs = [ctx.Process(target=_grad_worker, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    p, v, x, t0, tp, t1 = _grad_batch()
+    loss, g = omlp.loss_grad(p, v, x, t0, tp, t1)
+    for r in range(world):
+        lr, gr = out[r]
+        assert abs(lr - loss) <= 1e-12 * abs(loss)
+        assert np.allclose(gr, g, rtol=1e-12, atol=1e-15 * np.abs(g).max())
+    # without a process group the arguments come back unchanged
+    l1, g1 = D.all_reduce_gradient(loss, g, v.size)
+    assert l1 == loss and np.array_equal(g1, g)
