@@ -53,6 +53,12 @@ MIXED_LOG_EPS = -20.0
 FP32_OPS_PER_BIN = 35.92
 MUFU_OPS_PER_BIN = 4
 FP32_OPS_PER_PAIR = 505.1
+# XU-pipe (MUFU) operations per pair outside the bins, from the same captures
+# (smsp__inst_executed_pipe_xu: 46.5 per pair at 1 bin, 4.0 per bin), and the XU pipe's lanes per
+# SM per clock that ncu's XU percentages are taken against (170.5 operations per pair in 0.330 ms
+# per 4M pairs read as 23.2 % there).
+MUFU_OPS_PER_PAIR = 38.5
+XU_LANES_PER_SM = 32
 # DRAM bytes per pair of the fast-path kernel, from one ncu capture (50.39 MB read + 4.96 MB
 # written for 4,194,304 pairs; profiles/kv_mlp_tc_kernel_hard_band_4M.md), scaled to a launch.
 # Set to None whenever the kernel changes until it is captured again.
@@ -169,6 +175,18 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def sfu_utilisation(n_pairs, bins, launch_ms, sms, sm_mhz):
+    """XU (MUFU: ex2, lg2, rcp) operations per second of the fast-path kernel against the XU
+    pipe's peak, the second half of the metric's "% of FP32/SFU peak"."""
+    ops = n_pairs * (MUFU_OPS_PER_PAIR + (bins + 1) * MUFU_OPS_PER_BIN)
+    achieved = ops / (launch_ms / 1e3)
+    peak = sms * XU_LANES_PER_SM * sm_mhz * 1e6
+    return {"achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "T XU ops/s",
+            "frac": achieved / peak,
+            "peak_source": f"{sms} SMs x {XU_LANES_PER_SM} XU lanes x {sm_mhz:.0f} MHz (the XU-pipe peak "
+                           f"ncu's pipe percentages use)"}
 
 
 def end_to_end(args, vf, xf, mlp, dist, dev, world):
@@ -323,6 +341,7 @@ def main():
                    "l2": "inputs 134 MB + outputs 201 MB per step, larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
+        "sfu": sfu_utilisation(n_pairs, args.bins, launch_ms, sms, sm_mhz) if args.bracket == "mlp" else None,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk,

@@ -14,6 +14,11 @@ def test_bench_module_imports_and_defines_counts():
 
     assert bench.FP32_OPS_PER_BIN > 0 and bench.FP32_OPS_PER_PAIR > 0
     assert callable(bench._env_rank) and callable(bench.all_reduce_scalar)
+    # the SFU figure of the 16.7M-pair step at 32 bins, 1.273 ms, 152 SMs at 2070 MHz
+    s = bench.sfu_utilisation(16_777_216, 32, 1.273, 152, 2070.0)
+    assert set(s) >= {"achieved", "peak", "unit", "frac", "peak_source"}
+    assert abs(s["peak"] - 152 * 32 * 2070e6 / 1e12) < 1e-9
+    assert 0.2 < s["frac"] < 0.25 and abs(s["frac"] - s["achieved"] / s["peak"]) < 1e-12
 
 
 def test_reference_arm_prints_one_json_line():
