@@ -2,13 +2,25 @@
 
 One step = one pass of the whole hot path over the 16,777,216-pair hard-band workload
 (75 % v ~ U[0, 50], x log-uniform in [1e-3, 1e3]; 25 % |v - x| < 0.1 v), float32 I/O, mixed path:
-bracket (learned MLP with plain fallback, or the plain FP64 bracket), FP32 peak-relative bins,
-log K, d/dv, d/dx, and the backward epilogue (the derivatives multiplied by an incoming
-gradient).  Inputs are resident in HBM before timing; the working set (134 MB in, 201 MB out) is
-larger than L2.
+bracket (learned MLP with plain fallback), FP32 peak-relative bins, log K, d/dv, d/dx, and the
+backward epilogue (the derivatives multiplied by an incoming gradient).  Inputs are resident in
+HBM before timing; the working set (134 MB in + 67 MB gradient, 201 MB out) is larger than L2.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--bins 32] [--bracket mlp|plain]
+After the timed steps (outside the timed region) the outputs of the last timed step are checked
+on a seeded sample against the oracle's fixed-bin method in long double at the same bins and eps;
+the line carries the errors and the run exits non-zero if any exceeds the accuracy bound.  The
+default run also times, each with its own accuracy sample: the learned path at 64 and 128 bins,
+the plain FP32 bracket at the headline's bins (the method without the network at its fastest) and
+the FP64 path at 128 bins on a slice of the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--bins 32]
+    python bench.py --path learned|plain|f32|second|f64 [--workload hard_band|uniform_small]
+                    [--pairs P] [--no-cpu-baseline] [--no-e2e] [--no-accuracy] [--no-sweep]
     python bench.py --impl reference ...   # the CPU oracle on the host cores (baseline arm)
+
+`--path` selects the timed step (profiling cases): learned = the learned-bracket fast path (the
+headline), plain = the mixed path with the FP64 bracket, f32 = Algorithms 1-3 in FP32, second =
+the learned path with second derivatives, f64 = the FP64 path (float64 I/O).
 
 Under torchrun each rank runs its own replica of the workload (pairs are independent: weak
 scaling, no collective on the data path); rank 0 prints one JSON line.
@@ -16,7 +28,9 @@ scaling, no collective on the data path); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -38,6 +52,16 @@ UNIT = "pairs/s"
 N_PAIRS = 16_777_216
 WORKLOAD = "hard_band_16M"
 MIXED_LOG_EPS = -20.0
+F64_LOG_EPS = -52.0 * math.log(2.0)
+TOL_MIXED = 2e-6
+TOL_F64 = 1e-13
+# accuracy samples: the headline step's, and each extra entry's
+ACC_SAMPLE = 65_536
+ACC_SAMPLE_EXTRA = 16_384
+ACC_SAMPLE_F64 = 4_096
+ACC_EDGE = 256          # the first and last pairs always belong to the sample
+ACC_FALLBACK_MAX = 8_192
+F64_SLICE = 1 << 23     # the FP64 path's slice of the workload (134 MB of float64 inputs, larger than L2)
 
 # Algorithmic FP32 work of the learned-bracket fast path, counted operation by operation from
 # its formulas with an FMA as one operation and a paired (f32x2) instruction as two:
@@ -48,21 +72,48 @@ MIXED_LOG_EPS = -20.0
 #   per pair: layer 1 and layer 3 on the CUDA cores 256 (layer 2 runs on the tensor cores and
 #             is not counted), peak Newton, offset constants, endpoint check, setup and finish
 #             ~250                                                              -> 505
-# ncu's executed FFMA + FADD + FMUL (+ 2 x FFMA2/FADD2/FMUL2) counters over 4M pairs at 1 and 32
-# bins give 35.92 per bin and 505.1 per pair (profiles/kv_mlp_tc_kernel_hard_band_4M.md).
+# ncu's executed FFMA + FADD + FMUL (+ 2 x FFMA2/FADD2/FMUL2) counters over 4M hard-band pairs at
+# 1 and 32 bins (one launch of the fast-path kernel each) give 35.92 per bin and 505.1 per pair.
 FP32_OPS_PER_BIN = 35.92
 MUFU_OPS_PER_BIN = 4
 FP32_OPS_PER_PAIR = 505.1
-# XU-pipe (MUFU) operations per pair outside the bins, from the same captures
+# XU-pipe (MUFU) operations per pair outside the bins from the same captures
 # (smsp__inst_executed_pipe_xu: 46.5 per pair at 1 bin, 4.0 per bin), and the XU pipe's lanes per
 # SM per clock that ncu's XU percentages are taken against (170.5 operations per pair in 0.330 ms
-# per 4M pairs read as 23.2 % there).
+# per 4M pairs read as 23.3 % there).
 MUFU_OPS_PER_PAIR = 38.5
 XU_LANES_PER_SM = 32
-# DRAM bytes per pair of the fast-path kernel, from one ncu capture (50.39 MB read + 4.96 MB
-# written for 4,194,304 pairs; profiles/kv_mlp_tc_kernel_hard_band_4M.md), scaled to a launch.
-# Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES_PER_PAIR = (50.386688e6 + 4.958464e6) / 4194304
+# DRAM bytes per pair of the fast-path kernel from an ncu capture of one launch (read + write),
+# or None until one is taken for the current kernel.  The algorithmic bytes per pair are
+# v, x, grad_out in and log K, d/dv, d/dx out, 4 bytes each.
+TRAFFIC_BYTES_PER_PAIR = None
+ALGORITHMIC_BYTES_PER_PAIR = 24
+# The counts above hold for the fast-path kernel built from these sources; COUNTS_SOURCE_SHA is
+# their hash when the counts were taken.  When the sources change, the line says so and reports
+# no traffic until the counters are taken again.
+COUNTS_SOURCES = ("kv_mlp.cu", "kv_bins.cuh", "kv_dfloat.cuh", "kv_bracket_f32.cuh")
+COUNTS_SOURCE_SHA = "e68e9b9e5c42eab8"
+
+PATHS = {
+    # name: (bracket, second derivatives, float64 I/O)
+    "learned": ("mlp", False, False),
+    "plain": ("plain", False, False),
+    "f32": ("f32", False, False),
+    "second": ("mlp", True, False),
+    "f64": ("plain", False, True),
+}
+KERNEL_OF = {"learned": "kv_mlp_tc_kernel", "second": "kv_mlp_tc_kernel", "plain": "kv_mixed_kernel",
+             "f32": "kv_plain_f32_kernel", "f64": "kv_f64_kernel"}
+WORKLOADS = {"hard_band": (lambda n, seed: W.hard_band(n, seed=seed), N_PAIRS, 1),
+             "uniform_small": (lambda n, seed: W.uniform_small(n, seed=seed), 4096, 0)}
+
+
+def counts_source_sha() -> str:
+    h = hashlib.sha256()
+    for s in COUNTS_SOURCES:
+        with open(os.path.join(ROOT, "paper_2108_11560_gb300", "csrc", s), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def _peaks():
@@ -189,6 +240,61 @@ def sfu_utilisation(n_pairs, bins, launch_ms, sms, sm_mhz):
                            f"ncu's pipe percentages use)"}
 
 
+def fp32_roofline(n_pairs, bins, launch_ms, sms, sm_mhz, peak_src):
+    """Algorithmic FP32 operations of the fast-path kernel per launch over its launch time,
+    against the FP32 pipe's peak (128 lanes per SM per clock, an FMA counted as one operation)."""
+    ops = n_pairs * (FP32_OPS_PER_PAIR + (bins + 1) * FP32_OPS_PER_BIN)
+    achieved = ops / (launch_ms / 1e3)
+    peak = sms * 128 * sm_mhz * 1e6
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+            "unit": "Tops/s (FP32 pipe, FMA = 1 op)", "frac": achieved / peak,
+            "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_src} max clock)"}
+
+
+def sample_indices(n, k, seed, extra=()):
+    """A seeded sample of k indices of [0, n), with the first and last ACC_EDGE indices and the
+    given extra ones added."""
+    rng = np.random.default_rng(seed)
+    parts = [np.arange(min(ACC_EDGE, n)), np.arange(max(n - ACC_EDGE, 0), n),
+             rng.choice(n, min(k, n), replace=False)]
+    extra = np.asarray(extra, dtype=np.int64)
+    if extra.size > ACC_FALLBACK_MAX:
+        extra = rng.choice(extra, ACC_FALLBACK_MAX, replace=False)
+    parts.append(extra)
+    return np.unique(np.concatenate(parts).astype(np.int64))
+
+
+def accuracy(outs, v64, x64, idx, bins, log_eps, bound, grad_out=None):
+    """Maximum errors of the GPU outputs at the sampled indices against the oracle's fixed-bin
+    method in long double at the same bins and eps (the errors of Sec. 3.1 taken relative:
+    |d log K| / max(1, |log K|); plain relative errors for the derivatives, which must be exactly
+    0 at v = 0)."""
+    import torch
+
+    import oracle
+
+    it = torch.from_numpy(idx).to(outs["logk"].device)
+    g = {k: outs[k].index_select(0, it).double().cpu().numpy() for k in ("logk", "dv", "dx")}
+    if grad_out is not None:  # the fused epilogue multiplied the derivatives by grad_out
+        go = grad_out.index_select(0, it).double().cpu().numpy()
+        g["dv"] = g["dv"] / go
+        g["dx"] = g["dx"] / go
+    t = time.perf_counter()
+    ref = oracle.o1(v64[idx], x64[idx], bins=bins, log_eps=log_eps, precision="long")
+    secs = time.perf_counter() - t
+    e_l = np.abs(g["logk"] - ref["logk"]) / np.maximum(1.0, np.abs(ref["logk"]))
+    z = v64[idx] == 0.0
+    e_v = np.where(z, np.where(g["dv"] == 0.0, 0.0, np.inf),
+                   np.abs(g["dv"] - ref["dv"]) / np.maximum(np.abs(ref["dv"]), 1e-300))
+    e_x = np.abs(g["dx"] - ref["dx"]) / np.maximum(np.abs(ref["dx"]), 1e-300)
+    worst = max(float(e_l.max()), float(e_v.max()), float(e_x.max()))
+    return {"max_rel_logk": float(e_l.max()), "max_rel_dv": float(e_v.max()),
+            "max_rel_dx": float(e_x.max()), "pairs": int(idx.size), "bound": bound,
+            "ok": bool(worst <= bound),
+            "reference": f"oracle O1 in long double, {bins} bins, log eps {log_eps:.4g}",
+            "oracle_s": round(secs, 2)}
+
+
 def end_to_end(args, vf, xf, mlp, dist, dev, world):
     """The same call through the host-buffer entry point on pinned host buffers, inside the timed
     region (wall clock around the blocking call): the inputs cross to the GPU and the results
@@ -203,7 +309,7 @@ def end_to_end(args, vf, xf, mlp, dist, dev, world):
     hx = torch.from_numpy(xf).pin_memory().numpy()
     hout = tuple(torch.empty(n, dtype=torch.float32).pin_memory().numpy() for _ in range(3))
     steps = max(3, min(args.steps, 5))
-    kw = dict(bins=args.bins, bracket=args.bracket, mlp=mlp, out=hout, transfer=args.e2e_transfer)
+    kw = dict(bins=args.bins, bracket="mlp", mlp=mlp, out=hout, transfer=args.e2e_transfer)
     kv.kv_fwd_bwd_host(hv, hx, **kw)
     if dist:
         dist.barrier()
@@ -221,22 +327,108 @@ def end_to_end(args, vf, xf, mlp, dist, dev, world):
             "host_buffers": "pinned (torch pin_memory)"}
 
 
+def timed_steps(step, steps, warmup, stream):
+    """CUDA-event times (ms) of `steps` calls of step() after `warmup` untimed ones."""
+    import torch
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda._sleep(1 << 21)  # the GPU is busy while the host enqueues the first timed step
+    ev[0].record(stream)
+    for k in range(steps):
+        step()
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    return ev[0].elapsed_time(ev[-1]), [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+
+
+def fallback_pairs(kv, vt, xt, kw):
+    """Indices of the pairs that fell back to the plain bracket (status bit) and the rate, from
+    one more untimed call with the same arguments (the results are deterministic)."""
+    import torch
+
+    from paper_2108_11560_gb300 import _native as N
+
+    s = kv.kv_fwd_bwd_ex(vt, xt, status=True, **kw)["status"]
+    fb = torch.nonzero((s & N.KV_PAIR_FALLBACK) != 0).flatten().cpu().numpy()
+    return fb, fb.size / max(vt.numel(), 1)
+
+
+def extra_entries(args, kv, mlp, vf, xf, v64c, x64c, dev, stream, sms, sm_mhz, peak_src, check):
+    """The sweep of the learned path over 64 and 128 bins, the plain FP32 bracket at the headline's
+    bins and the FP64 path at 128 bins on a slice, each timed with CUDA events and each with its
+    own accuracy sample."""
+    import torch
+
+    n = vf.size
+    vt = torch.from_numpy(vf).to(dev)
+    xt = torch.from_numpy(xf).to(dev)
+    out = {k: torch.empty(n, dtype=torch.float32, device=dev) for k in ("logk", "dv", "dx")}
+    res = {"sweep": {}, "f32_bracket": None, "fp64_plain": None}
+    runs = [("mlp", b) for b in (64, 128) if b != args.bins] + [("f32", args.bins)]
+    for bracket, bins in runs:
+        kw = dict(bins=bins, bracket=bracket, mlp=mlp if bracket == "mlp" else None)
+        total, _ = timed_steps(lambda: kv.kv_fwd_bwd_ex(vt, xt, out=out, **kw), args.steps, args.warmup, stream)
+        ms = total / args.steps
+        e = {"bins": bins, "value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "pairs": n}
+        if bracket == "mlp":
+            e["frac_fp32"] = fp32_roofline(n, bins, ms, sms, sm_mhz, peak_src)["frac"]
+        if check:
+            fb, rate = fallback_pairs(kv, vt, xt, kw)
+            e["fallback_rate"] = rate
+            idx = sample_indices(n, ACC_SAMPLE_EXTRA, 1000 + bins, fb)
+            e["accuracy"] = accuracy(out, v64c, x64c, idx, bins, MIXED_LOG_EPS, TOL_MIXED)
+        if bracket == "mlp":
+            res["sweep"][str(bins)] = e
+        else:
+            e["kernel"] = KERNEL_OF["f32"]
+            res["f32_bracket"] = e
+    del vt, xt, out
+    # the FP64 path on the first F64_SLICE pairs (the float32-cast inputs in double)
+    m = min(F64_SLICE, n)
+    v64t = torch.from_numpy(v64c[:m].copy()).to(dev)
+    x64t = torch.from_numpy(x64c[:m].copy()).to(dev)
+    o64 = {k: torch.empty(m, dtype=torch.float64, device=dev) for k in ("logk", "dv", "dx")}
+    total, _ = timed_steps(lambda: kv.kv_fwd_bwd_ex(v64t, x64t, bins=128, out=o64), max(2, args.steps // 3),
+                           args.warmup, stream)
+    ms = total / max(2, args.steps // 3)
+    e = {"bins": 128, "value": m / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "pairs": m,
+         "slice": f"first {m} pairs of the workload, float64 I/O", "kernel": KERNEL_OF["f64"]}
+    if check:
+        idx = sample_indices(m, ACC_SAMPLE_F64, 2000)
+        e["accuracy"] = accuracy(o64, v64c[:m], x64c[:m], idx, 128, F64_LOG_EPS, TOL_F64)
+    res["fp64_plain"] = e
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--bins", type=int, default=32)
-    ap.add_argument("--bracket", choices=("mlp", "plain"), default="mlp")
+    ap.add_argument("--bins", type=int, default=0, help="0: 32 (128 on the FP64 path)")
+    ap.add_argument("--path", choices=tuple(PATHS), default="learned")
+    ap.add_argument("--bracket", choices=("mlp", "plain", "f32"), default=None,
+                    help="the same as --path learned|plain|f32")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="hard_band")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the accuracy samples (profiling runs)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the extra timed entries (profiling runs)")
     ap.add_argument("--e2e-transfer", choices=("auto", "staged", "direct"), default="auto",
                     help="how the host-buffer leg moves the data (kv_fwd_bwd_host_ex)")
-    ap.add_argument("--pairs", type=int, default=N_PAIRS, help="pairs per GPU (profiling runs)")
+    ap.add_argument("--pairs", type=int, default=0, help="pairs per GPU (0: the workload's size)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.bracket is not None:
+        args.path = {"mlp": "learned", "plain": "plain", "f32": "f32"}[args.bracket]
+    bracket, second, f64io = PATHS[args.path]
+    if args.bins == 0:
+        args.bins = 128 if f64io else 32
     if args.impl == "reference":
         return run_reference(args)
 
@@ -253,22 +445,31 @@ def main():
     from paper_2108_11560_gb300 import kv
 
     lib = N.lib()
-    n_pairs = args.pairs
-    v64, x64 = W.hard_band(n_pairs, seed=1 + 1000 * rank)
-    vf = v64.astype(np.float32)
-    xf = x64.astype(np.float32)
+    gen, default_n, seed = WORKLOADS[args.workload]
+    n_pairs = args.pairs or default_n
+    headline = args.path == "learned" and args.workload == "hard_band"
+    v64, x64 = gen(n_pairs, seed + 1000 * rank)
+    io = np.float64 if f64io else np.float32
+    vf = v64.astype(io)
+    xf = x64.astype(io)
+    # the inputs the GPU sees, in double, for the oracle
+    v64c = vf.astype(np.float64)
+    x64c = xf.astype(np.float64)
+    tdt = torch.float64 if f64io else torch.float32
     vt = torch.from_numpy(vf).to(dev)
     xt = torch.from_numpy(xf).to(dev)
-    go = torch.ones(n_pairs, dtype=torch.float32, device=dev)
-    outs = {k: torch.empty(n_pairs, dtype=torch.float32, device=dev) for k in ("logk", "dv", "dx")}
+    go = torch.ones(n_pairs, dtype=tdt, device=dev)
+    outs = {k: torch.empty(n_pairs, dtype=tdt, device=dev) for k in ("logk", "dv", "dx")}
+    if second:
+        outs.update({k: torch.empty(n_pairs, dtype=tdt, device=dev) for k in ("d2v", "dvx", "d2x")})
     mlp = None
-    if args.bracket == "mlp":
+    if bracket == "mlp":
         from paper_2108_11560_gb300 import learned
         mlp = learned.default_network(dev)
+    kw = dict(bins=args.bins, bracket=bracket, mlp=mlp, second=second)
 
     def step():
-        kv.kv_fwd_bwd_ex(vt, xt, bins=args.bins, bracket=args.bracket, mlp=mlp, grad_out=go,
-                         out=outs)
+        kv.kv_fwd_bwd_ex(vt, xt, grad_out=None if second else go, out=outs, **kw)
 
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
@@ -301,7 +502,7 @@ def main():
 
     # end to end: the same call on pinned host buffers, copies inside the timed region
     e2e = None
-    if not args.no_e2e:
+    if headline and not args.no_e2e:
         e2e = end_to_end(args, vf, xf, mlp, dist, dev, world)
     if rank != 0:
         if dist:
@@ -311,48 +512,74 @@ def main():
     clk = clocks.summary()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    # FP32 pipe: 128 lanes per SM per clock (an FMA counted as one operation), at the max SM clock
-    peak_ops = sms * 128 * sm_mhz * 1e6
     launch_ms = total_ms / args.steps
-    # the step's two launches: the fast-path kernel is > 99.8 % of the GPU time (launch list in
-    # profiles/launches_bench_hard_band_16M.md), so its launch time is taken as the step time
-    if args.bracket == "mlp":
-        ops = n_pairs * (FP32_OPS_PER_PAIR + (args.bins + 1) * FP32_OPS_PER_BIN)
-        traffic = (n_pairs * TRAFFIC_BYTES_PER_PAIR) if TRAFFIC_BYTES_PER_PAIR else None
-        kernel = "kv_mlp_tc_kernel"
-    else:  # the plain path is bound by the FP64 bracket; only its FP32 bins are counted
-        ops = n_pairs * (args.bins + 1) * FP32_OPS_PER_BIN
-        traffic = None
-        kernel = "kv_mixed_kernel"
-    achieved = ops / (launch_ms / 1e3)
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                "unit": "Tops/s (FP32 pipe, FMA = 1 op)", "frac": achieved / peak_ops,
-                "traffic": traffic, "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz "
-                                                      f"({peak_src} max clock)",
-                "kernel": kernel}
+    check = not args.no_accuracy
+    acc = None
+    fb_rate = None
+    if check:
+        # the last timed step's outputs, on a seeded sample with the fallback pairs added
+        fb = np.zeros(0, dtype=np.int64)
+        if bracket == "mlp":
+            fb, fb_rate = fallback_pairs(kv, vt, xt, kw)
+        idx = sample_indices(n_pairs, ACC_SAMPLE, 7, fb)
+        acc = accuracy(outs, v64c, x64c, idx, args.bins, F64_LOG_EPS if f64io else MIXED_LOG_EPS,
+                       TOL_F64 if f64io else TOL_MIXED, grad_out=None if second else go)
+        acc["fallback_rate"] = fb_rate
+    sha = counts_source_sha()
+    counts_current = sha == COUNTS_SOURCE_SHA
+    roofline = None
+    sfu = None
+    if bracket == "mlp" and not second:
+        # the step's two launches: the fast-path kernel is > 99.8 % of the GPU time (ncu launch
+        # list of this command), so its launch time is taken as the step time
+        roofline = fp32_roofline(n_pairs, args.bins, launch_ms, sms, sm_mhz, peak_src)
+        roofline["traffic"] = (n_pairs * TRAFFIC_BYTES_PER_PAIR
+                               if (TRAFFIC_BYTES_PER_PAIR and counts_current) else None)
+        roofline["algorithmic_bytes"] = n_pairs * ALGORITHMIC_BYTES_PER_PAIR
+        roofline["kernel"] = KERNEL_OF[args.path]
+        roofline["counts_source_sha"] = sha
+        roofline["counts_current"] = counts_current
+        sfu = sfu_utilisation(n_pairs, args.bins, launch_ms, sms, sm_mhz)
+        sfu["counts_current"] = counts_current
+    io_desc = "float64" if f64io else "float32"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 bins + extended-precision peak/offset",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if f64io else "f32 bins + extended-precision peak/offset",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if n_pairs == N_PAIRS else f"hard_band_{n_pairs}",
-                   "pairs_per_gpu": n_pairs, "bins": args.bins,
-                   "bracket": args.bracket, "log_eps": MIXED_LOG_EPS, "io": "float32",
-                   "l2": "inputs 134 MB + outputs 201 MB per step, larger than L2 (no flush)",
+        "config": {"workload": WORKLOAD if headline and n_pairs == N_PAIRS else f"{args.workload}_{n_pairs}",
+                   "pairs_per_gpu": n_pairs, "bins": args.bins, "path": args.path,
+                   "bracket": bracket, "second_derivatives": second,
+                   "log_eps": F64_LOG_EPS if f64io else MIXED_LOG_EPS, "io": io_desc,
+                   "l2": "inputs 134 MB + outputs 201 MB per step, larger than L2 (no flush)"
+                         if n_pairs >= N_PAIRS else "profiling case",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
-        "sfu": sfu_utilisation(n_pairs, args.bins, launch_ms, sms, sm_mhz) if args.bracket == "mlp" else None,
+        "sfu": sfu,
+        "accuracy": acc,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk,
         "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
     }
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(v64.astype(np.float32).astype(np.float64),
-                                            x64.astype(np.float32).astype(np.float64), args.bins)
+    if headline and not args.no_sweep:
+        line.update(extra_entries(args, kv, mlp, vf, xf, v64c, x64c, dev, stream, sms, sm_mhz,
+                                  peak_src, check))
+        if line["f32_bracket"]:
+            line["learned_vs_f32_bracket"] = value / world / line["f32_bracket"]["value"]
+        if line["fp64_plain"]:
+            line["learned_vs_fp64_plain"] = value / world / line["fp64_plain"]["value"]
+    if world == 1 and not args.no_cpu_baseline and not f64io:
+        line["cpu_baseline"] = cpu_baseline(v64c, x64c, args.bins)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+    oks = [line["accuracy"]] + [e.get("accuracy") for e in line.get("sweep", {}).values()]
+    oks += [(line.get(k) or {}).get("accuracy") for k in ("f32_bracket", "fp64_plain")]
+    if any(a is not None and not a["ok"] for a in oks):
+        print("accuracy bound exceeded", file=sys.stderr)
+        return 3
     return 0
 
 

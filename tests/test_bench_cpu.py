@@ -48,3 +48,48 @@ def test_own_arm_fails_loudly_without_a_gpu():
                        capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode != 0
     assert not any(l.strip().startswith("{") for l in r.stdout.splitlines())
+
+
+def test_accuracy_certificate_catches_a_wrong_output():
+    """The bench's accuracy check (run after the timed steps on the GPU outputs) on CPU tensors:
+    outputs equal to the oracle's method pass, and one output moved by 1e-5 relative fails."""
+    import numpy as np
+    import pytest
+
+    torch = pytest.importorskip("torch")
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_2108_11560_gb300 import workloads as W
+
+    v, x = W.hard_band(3000, seed=41)
+    (vf, v64), (xf, x64) = W.to_f32(v, x)
+    v64[5] = 0.0
+    ref = oracle.o1(v64, x64, bins=32, log_eps=bench.MIXED_LOG_EPS, precision="long")
+    outs = {k: torch.tensor(ref[k], dtype=torch.float64) for k in ("logk", "dv", "dx")}
+    idx = bench.sample_indices(v64.size, 500, 3, extra=[7, 2999])
+    assert idx[0] == 0 and idx[-1] == v64.size - 1 and 7 in idx and 5 in idx
+    assert np.all(np.diff(idx) > 0)
+    a = bench.accuracy(outs, v64, x64, idx, 32, bench.MIXED_LOG_EPS, bench.TOL_MIXED)
+    assert a["ok"] and a["max_rel_logk"] < 1e-15 and a["pairs"] == idx.size
+    go = torch.full((v64.size,), 2.0, dtype=torch.float64)
+    scaled = dict(outs, dv=outs["dv"] * 2.0, dx=outs["dx"] * 2.0)
+    assert bench.accuracy(scaled, v64, x64, idx, 32, bench.MIXED_LOG_EPS, bench.TOL_MIXED, grad_out=go)["ok"]
+    bad = {k: t.clone() for k, t in outs.items()}
+    bad["dx"][7] *= 1.0 + 1e-5
+    b = bench.accuracy(bad, v64, x64, idx, 32, bench.MIXED_LOG_EPS, bench.TOL_MIXED)
+    assert not b["ok"] and 9e-6 < b["max_rel_dx"] < 1.1e-5
+    bad = {k: t.clone() for k, t in outs.items()}
+    bad["dv"][5] = 1e-30  # d/dv must be exactly 0 at v = 0
+    assert not bench.accuracy(bad, v64, x64, idx, 32, bench.MIXED_LOG_EPS, bench.TOL_MIXED)["ok"]
+
+
+def test_counts_source_hash_is_current_or_flagged():
+    """The ncu-derived operation counts are tied to the fast kernel's sources by a hash; the
+    bench reports whether they match (a stale count is reported as such, never silently)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    h = bench.counts_source_sha()
+    assert isinstance(h, str) and len(h) == 16
+    assert isinstance(bench.COUNTS_SOURCE_SHA, str) and len(bench.COUNTS_SOURCE_SHA) == 16
