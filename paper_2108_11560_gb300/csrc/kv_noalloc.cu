@@ -6,6 +6,9 @@
 // until the process exits.  All calls on a device share it: calls whose work overlaps on the GPU
 // (different streams without ordering between them) race on it and must be serialised by the
 // caller.  The partial sums are fully overwritten by each call, so nothing needs clearing.
+// The array's device address is looked up once per device and kept for the life of the process:
+// a cudaDeviceReset, or anything else that destroys the device's primary context, invalidates it,
+// so the entry point must not be used on a device after such a reset.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -43,6 +46,10 @@ int scratch_address(double** out)
     return KV_OK;
 }
 
+// partial_sums and final_sum repeat kv_sum's two kernels (kv_sum_partial and kv_sum_final in
+// kv_core.cu) with the same block size, per-block stride and reduction order; with the same
+// number of blocks (every n up to 4,194,304 elements, where kv_sum uses one block per 4096) the
+// two entry points give the same bits.  A change to either pair must be made to both.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) partial_sums(const T* a, int64_t n, double* part)
 {

@@ -36,7 +36,7 @@ def all_reduce_scalar(value: float, op: str = "sum", device=None) -> float:
 
     if not (dist.is_available() and dist.is_initialized()):
         return float(value)
-    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=_collective_device(device))
     dist.all_reduce(t, op={"sum": dist.ReduceOp.SUM, "max": dist.ReduceOp.MAX}[op])
     return float(t.item())
 
@@ -48,13 +48,28 @@ def sharded_loglik(v, x, rank: int, world: int, local_sum, device=None) -> float
     return all_reduce_scalar(float(local_sum(v[lo:hi], x[lo:hi])), "sum", device)
 
 
+def _collective_device(device):
+    """The device a collective's buffer must live on: the given one, else the current CUDA device
+    under the NCCL backend (which takes only CUDA tensors), else the CPU."""
+    import torch
+    import torch.distributed as dist
+
+    if device is not None:
+        return torch.device(device)
+    if dist.get_backend() == "nccl":
+        return torch.device("cuda", torch.cuda.current_device())
+    return torch.device("cpu")
+
+
 def all_reduce_gradient(loss: float, grad, count: int, device=None):
     """Mean loss and gradient over a batch split across ranks: each rank passes the mean loss and
     gradient over its `count` samples (on a GPU: kv_mlp_loss_grad on its share), and the
-    count-weighted sums meet in one all-reduce, so every rank gets the full batch's mean (the
-    data-parallel step of training the learned bracket; ~4.5k parameters).  Without a process
-    group the arguments come back unchanged.  Returns (loss, grad) with grad shaped like the
-    input, in float64."""
+    count-weighted sums meet in one all-reduce, so every rank gets the full batch's mean.  This is
+    the exchange a data-parallel training step of the learned bracket needs (~4.5k parameters); it
+    is a host-side helper, not wired into Mlp.train (training runs on one GPU).  The buffer goes
+    to `device`, or by default to the current CUDA device under NCCL and the CPU under gloo.
+    Without a process group the arguments come back unchanged.  Returns (loss, grad) with grad
+    shaped like the input, in float64."""
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -63,8 +78,7 @@ def all_reduce_gradient(loss: float, grad, count: int, device=None):
         return float(loss), np.asarray(grad, dtype=np.float64)
     g = torch.as_tensor(np.asarray(grad, dtype=np.float64)).reshape(-1)
     buf = torch.cat([g * float(count), torch.tensor([float(loss) * count, float(count)], dtype=torch.float64)])
-    if device is not None:
-        buf = buf.to(device)
+    buf = buf.to(_collective_device(device))
     dist.all_reduce(buf)
     buf = buf.cpu()
     total = float(buf[-1])

@@ -108,6 +108,8 @@ def _grad_worker(rank, world, port, out):
         p, v, x, t0, tp, t1 = _grad_batch()
         lo, hi = D.shard_bounds(v.size, rank, world)  # unequal shares: 151 and 150 samples
         loss, g = omlp.loss_grad(p, v[lo:hi], x[lo:hi], t0[lo:hi], tp[lo:hi], t1[lo:hi])
+        # the collective's buffer goes to the CPU under gloo (to the current GPU under NCCL)
+        assert D._collective_device(None).type == "cpu"
         out[rank] = D.all_reduce_gradient(loss, g, hi - lo)
     finally:
         dist.destroy_process_group()
