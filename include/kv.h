@@ -121,7 +121,9 @@ typedef struct kv_args {
     int bracket;          /* enum kv_bracket_mode */
     double log_eps;       /* log of the range's eps (< 0); 0 = the dtype's default */
     int max_iter;         /* FindZero iterations; 0 = KV_DEFAULT_MAX_ITER */
-    int lanes;            /* lanes that share one pair's bins (1, 2, 4, 8, 16, 32); 0 = automatic */
+    int lanes;            /* lanes that share one pair's bins on the FP64-bracket paths (1, 2, 4, 8,
+                           * 16, 32): every lane brackets its own pair, then groups of `lanes`
+                           * lanes sum the pairs' bins in `lanes` rounds; 0 = automatic (1) */
     const kv_mlp* mlp;    /* network for KV_BRACKET_MLP, else ignored */
     uint8_t* status;      /* [n] or NULL: per-pair kv_pair_status bits */
     unsigned long long* fallback_count; /* device counter or NULL: += pairs that fell back */
@@ -134,7 +136,20 @@ typedef struct kv_args {
     void* d2v;
     void* dvx;
     void* d2x;
+    int flags;            /* enum kv_flag bits; 0 = the paper's algorithms throughout */
 } kv_args;
+
+/* Options of kv_fwd_bwd_ex (kv_args.flags).  Unknown bits give KV_ERR_ARG. */
+enum kv_flag {
+    /* Not in the paper: the FP64 bracket's peak search (Sec. 2.2) skips Algorithm 1's doublings
+     * and runs Algorithm 2 on the analytic bracket [0, asinh(v/x)] (g'(0) = 0, and
+     * g'(asinh(v/x)) = v tanh(vt) - v < 0), falling back to the doublings where g' is not
+     * negative there in rounded arithmetic.  Applies wherever the plain FP64 bracket runs
+     * (KV_BRACKET_PLAIN, and the learned path's FP64 fallback); kv_bracket() always follows
+     * Algorithms 1-3.  The peak then differs from Algorithms 1-2's within their convergence, which
+     * moves the results only at the level of the method's own error. */
+    KV_FLAG_PEAK_ANALYTIC_START = 1
+};
 
 /* Per-pair status bits written to kv_args.status. */
 enum kv_pair_status {
@@ -221,7 +236,9 @@ int kv_sum(const void* a, int64_t n, int dtype, double* out, void* stream);
  *     process exits).  n > KV_SUM_NOALLOC_MAX_N returns KV_ERR_SIZE before any GPU work.
  *   - The call allocates and frees nothing.  Its first call on a device looks up the array's
  *     device address (cudaGetSymbolAddress), once per device; make that first call before any
- *     stream capture.
+ *     stream capture.  The address is kept for the life of the process: after a
+ *     cudaDeviceReset (or anything else that destroys the device's primary context) this entry
+ *     point must not be called on that device again.
  *   - All calls on a device share the array: calls whose work can overlap on the GPU (streams
  *     with no ordering between them) race on it, so the caller must order them.  Each call
  *     overwrites the partial sums it uses, so nothing needs clearing between calls.

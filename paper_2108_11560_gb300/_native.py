@@ -25,6 +25,7 @@ KV_MLP_NPARAMS = 4482
 KV_SUM_NOALLOC_MAX_N = 67108864
 KV_PAIR_OK, KV_PAIR_EDGE, KV_PAIR_FALLBACK, KV_PAIR_RANGE_CAP = 0, 1, 2, 4
 KV_HOST_AUTO, KV_HOST_STAGED, KV_HOST_DIRECT = 0, 1, 2
+KV_FLAG_PEAK_ANALYTIC_START = 1
 
 #: every function include/kv.h declares
 EXPORTED = [
@@ -46,6 +47,7 @@ class KvArgs(ctypes.Structure):
         ("lanes", ctypes.c_int), ("mlp", ctypes.c_void_p), ("status", ctypes.c_void_p),
         ("fallback_count", ctypes.c_void_p), ("stream", ctypes.c_void_p),
         ("d2v", ctypes.c_void_p), ("dvx", ctypes.c_void_p), ("d2x", ctypes.c_void_p),
+        ("flags", ctypes.c_int),
     ]
 
 

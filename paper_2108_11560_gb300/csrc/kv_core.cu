@@ -1,10 +1,14 @@
 // Core kernels and C-ABI entry points of the batched log K_v(x) library (see include/kv.h).
 //
-// One (v, x) pair is handled by a group of L lanes of one warp (L = 1 for large batches): every
-// lane runs the pair's bracket (Algorithms 1-3, FP64) and then its share of the bins (Sec. 2.4,
-// Sec. 4.1); the partial sums meet by warp shuffles.  Warps iterate over pair groups in a
+// A warp takes 32 / L consecutive (v, x) pairs per trip and gives each a group of L lanes.  The
+// group runs its pair's bracket (Algorithms 1-3, FP64) together, its lanes evaluating several
+// points of each search at once (kv_bracket.cuh), then shares the pair's bins (Sec. 2.4,
+// Sec. 4.1) and reduces its partial sums by warp shuffles.  L = 1 (large batches) is one pair per
+// lane throughout; small batches take L > 1 so that they still occupy several warps per SM:
+// GB300's FP64 unit costs the same per warp instruction whatever the number of active lanes, and
+// one warp uses one SM sub-partition's share of it.  Warps iterate over pair blocks in a
 // grid-stride loop so that all lanes of a warp make the same number of trips (the shuffles need
-// the whole warp); pairs past the end are computed on dummy inputs and not stored.
+// the whole group); pairs past the end are computed on dummy inputs and not stored.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -129,6 +133,7 @@ struct KParams {
     int bins;
     double log_eps;
     int max_iter;
+    int flags;
 };
 
 // Domain edge cases (the list at the top of kv.h).  Returns true and fills the outputs for an
@@ -160,9 +165,26 @@ __device__ __forceinline__ bool edge_pair(double v, double x, double& lk, double
     return false;
 }
 
-__device__ __noinline__ BracketD bracket_call(double v, double x, double log_eps, int max_iter)
+__device__ __noinline__ BracketD bracket_call(double v, double x, double log_eps, int max_iter, int flags)
 {
-    return bracket_f64(v, x, log_eps, max_iter);
+    return bracket_f64(v, x, log_eps, max_iter, (flags & KV_FLAG_PEAK_ANALYTIC_START) != 0);
+}
+
+// The bracket of this lane's pair: on the lane alone (L = 1), or on the L lanes of its group,
+// which all hold the same pair (L >= 2).
+template <int L>
+__device__ __forceinline__ BracketD bracket_lanes(double v, double x, double log_eps, int max_iter, int flags)
+{
+    if constexpr (L == 1) {
+        return bracket_call(v, x, log_eps, max_iter, flags);
+    } else {
+        const int lane = threadIdx.x & 31;
+        LaneGroup G;
+        G.first = lane & ~(L - 1);
+        G.l = lane & (L - 1);
+        G.mask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u)) << G.first;
+        return bracket_f64_group<L>(G, v, x, log_eps, max_iter, (flags & KV_FLAG_PEAK_ANALYTIC_START) != 0);
+    }
 }
 
 template <typename T>
@@ -194,164 +216,213 @@ __device__ __forceinline__ void store_second(const KParams& p, int64_t i, double
     if (p.d2x) ((T*)p.d2x)[i] = (T)d2x;
 }
 
+// Per-pair state: bracket, bin constants and the inputs as given.
+struct SlotD {
+    BinsD b;
+    double G;           // g(t_p)
+    double vin, xin;    // the inputs as given (edge results and the sign of v)
+    double ar, cr;      // t_p tanh(v t_p), cosh t_p (second derivatives)
+    int flags;          // kSlot* bits
+};
+constexpr int kSlotActive = 1, kSlotEdge = 2, kSlotCapped = 4;
+
+// Pair i of this lane's group: the domain edges, the bracket (Algorithms 1-3) and the FP64 bin
+// constants (every lane of the group computes the same).
+template <int L>
+__device__ __forceinline__ SlotD bracket_slot_f64(const KParams& p, int64_t i)
+{
+    SlotD s;
+    const bool active = i < p.n;
+    s.vin = active ? ((const double*)p.v)[i] : 1.0;
+    s.xin = active ? ((const double*)p.x)[i] : 1.0;
+    double lk, dv, dx;
+    const bool edge = edge_pair(s.vin, s.xin, lk, dv, dx);
+    const double va = edge ? 1.0 : fabs(s.vin);
+    const double xa = edge ? 1.0 : s.xin;
+    BracketD br = bracket_lanes<L>(va, xa, p.log_eps, p.max_iter, p.flags);
+    BinsD& b = s.b;
+    b.v = va;
+    b.x = xa;
+    b.t0 = br.t0;
+    b.h = (br.t1 - br.t0) / p.bins;
+    b.tp = br.tp;
+    b.s0 = br.t0 - br.tp;
+    b.e2u = exp(-2.0 * va * br.tp);
+    b.Lu = log1p(b.e2u);
+    b.ep = exp(br.tp);
+    b.em = 1.0 / b.ep;
+    const double shp = sinh(br.tp);
+    b.c1 = fma(-xa, shp, va);
+    b.xch = xa * cosh(br.tp);
+    b.xsh = xa * shp;
+    b.shp = shp;
+    b.n = p.bins;
+    s.G = br.G;
+    s.ar = br.tp * ((1.0 - b.e2u) / (1.0 + b.e2u));
+    s.cr = cosh(br.tp);
+    s.flags = (active ? kSlotActive : 0) | (edge ? kSlotEdge : 0) | (br.capped ? kSlotCapped : 0);
+    return s;
+}
+
 // FP64 plain path: the paper's bracket and bins, all in double.  With D2 (L = 1 only) the bins
 // also give the second derivatives (sums2_f64), and the first derivatives come from the same
 // shifted sums.
 template <int L, bool DERIV, bool D2 = false>
 __global__ void __launch_bounds__(kBlock) kv_f64_kernel(KParams p)
 {
-    const int lane = threadIdx.x % L;
-    constexpr int G = 32 / L;  // pair groups per warp
-    const int g = (threadIdx.x % 32) / L;
+    static_assert(!D2 || L == 1, "second derivatives run one pair per lane");
+    constexpr int Q = 32 / L;  // pairs per warp trip (lane groups per warp)
+    const int lane = threadIdx.x & 31;
+    const int g = lane / L, l = lane % L;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
-    for (int64_t base = warp * G; base < p.n; base += nwarps * G) {
-        const int64_t i = base + g;
-        const bool active = i < p.n;
-        double v = active ? ((const double*)p.v)[i] : 1.0;
-        double x = active ? ((const double*)p.x)[i] : 1.0;
-        double lk, dv, dx;
-        const bool edge = edge_pair(v, x, lk, dv, dx);
-        const double va = edge ? 1.0 : fabs(v);
-        const double xa = edge ? 1.0 : x;
-        BracketD br = bracket_call(va, xa, p.log_eps, p.max_iter);
-        BinsD b;
-        b.v = va;
-        b.x = xa;
-        b.t0 = br.t0;
-        b.h = (br.t1 - br.t0) / p.bins;
-        b.tp = br.tp;
-        b.s0 = br.t0 - br.tp;
-        b.e2u = exp(-2.0 * va * br.tp);
-        b.Lu = log1p(b.e2u);
-        b.ep = exp(br.tp);
-        b.em = 1.0 / b.ep;
-        const double shp = sinh(br.tp);
-        b.c1 = fma(-xa, shp, va);
-        b.xch = xa * cosh(br.tp);
-        b.xsh = xa * shp;
-        b.shp = shp;
-        b.n = p.bins;
-        if constexpr (D2) {
-            const Sums2<double> m = sums2_f64<L>(b, lane);
-            if (active) {
-                double d2v, dvx, d2x;
-                uint8_t st = KV_PAIR_OK;
-                if (edge) {
-                    edge_second(x, d2v, dvx, d2x);
-                    st = KV_PAIR_EDGE;
-                } else {
-                    const double ar = br.tp * ((1.0 - b.e2u) / (1.0 + b.e2u));
-                    moments_finish<double>(m, ar, cosh(br.tp), dv, dx, d2v, dvx, d2x);
-                    lk = br.G + log(b.h) + log(m.s0);
-                    dv = v == 0.0 ? 0.0 : copysign(dv, v);
-                    dvx = v == 0.0 ? 0.0 : copysign(1.0, v) * dvx;
-                    if (br.capped) st = KV_PAIR_RANGE_CAP;
+    for (int64_t base = warp * Q; base < p.n; base += nwarps * Q) {
+        {
+            const int64_t i = base + g;  // the pair this lane's group brackets and sums together
+            const SlotD s = bracket_slot_f64<L>(p, i);
+            const bool active = s.flags & kSlotActive;
+            const bool edge = s.flags & kSlotEdge;
+            const uint8_t st = edge ? KV_PAIR_EDGE : (s.flags & kSlotCapped) ? KV_PAIR_RANGE_CAP : KV_PAIR_OK;
+            double lk, dv, dx;
+            edge_pair(s.vin, s.xin, lk, dv, dx);
+            if constexpr (D2) {
+                const Sums2<double> m = sums2_f64<1>(s.b, 0);
+                if (active) {
+                    double d2v, dvx, d2x;
+                    if (edge) {
+                        edge_second(s.xin, d2v, dvx, d2x);
+                    } else {
+                        moments_finish<double>(m, s.ar, s.cr, dv, dx, d2v, dvx, d2x);
+                        lk = s.G + log(s.b.h) + log(m.s0);
+                        dv = s.vin == 0.0 ? 0.0 : copysign(dv, s.vin);
+                        dvx = s.vin == 0.0 ? 0.0 : copysign(1.0, s.vin) * dvx;
+                    }
+                    store_outputs<double>(p, i, lk, dv, dx, st);
+                    store_second<double>(p, i, d2v, dvx, d2x);
                 }
-                store_outputs<double>(p, i, lk, dv, dx, st);
-                store_second<double>(p, i, d2v, dvx, d2x);
-            }
-            continue;
-        }
-        double S0, S1, S2;
-        sums_f64<L, DERIV>(b, lane, S0, S1, S2);
-        if (active && lane == 0) {
-            uint8_t st = KV_PAIR_OK;
-            if (edge) {
-                st = KV_PAIR_EDGE;
             } else {
-                lk = br.G + log(b.h) + log(S0);
-                dv = DERIV ? copysign(S1 / S0, v) : 0.0;
-                if (v == 0.0) dv = 0.0;
-                dx = DERIV ? -(S2 / S0) : 0.0;
-                if (br.capped) st = KV_PAIR_RANGE_CAP;
+                double S0, S1, S2;
+                sums_f64<L, DERIV>(s.b, l, S0, S1, S2);
+                if (active && l == 0) {
+                    if (!edge) {
+                        lk = s.G + log(s.b.h) + log(S0);
+                        dv = DERIV ? copysign(S1 / S0, s.vin) : 0.0;
+                        if (s.vin == 0.0) dv = 0.0;
+                        dx = DERIV ? -(S2 / S0) : 0.0;
+                    }
+                    store_outputs<double>(p, i, lk, dv, dx, st);
+                }
             }
-            store_outputs<double>(p, i, lk, dv, dx, st);
         }
     }
 }
 
+// Per-pair state of the mixed path with the FP64 bracket (FP32 bin constants, FP64 offset).
+struct SlotF {
+    BinsF b;
+    double G;
+    float vin, xin;
+    float ar, cr;  // second derivatives
+    int flags;
+};
+
+// Pair i of this lane's group on the mixed path: edges, the FP64 bracket, FP64 offset and
+// constants rounded to the FP32 bins' form.
+template <int L>
+__device__ __forceinline__ SlotF bracket_slot_mixed(const KParams& p, int64_t i)
+{
+    SlotF s;
+    const bool active = i < p.n;
+    s.vin = active ? ((const float*)p.v)[i] : 1.0f;
+    s.xin = active ? ((const float*)p.x)[i] : 1.0f;
+    double lk, dv, dx;
+    const bool edge = edge_pair((double)s.vin, (double)s.xin, lk, dv, dx);
+    const double va = edge ? 1.0 : fabs((double)s.vin);
+    const double xa = edge ? 1.0 : (double)s.xin;
+    BracketD br = bracket_lanes<L>(va, xa, p.log_eps, p.max_iter, p.flags);
+    const double ep = exp(br.tp), em = 1.0 / ep;
+    const double u = va * br.tp;
+    const double h = (br.t1 - br.t0) / p.bins;
+    const double e2u = exp(-2.0 * u);
+    BinsF& b = s.b;
+    b.s0 = (float)(br.t0 - br.tp);
+    b.h = (float)h;
+    b.v = (float)va;
+    b.u = (float)u;
+    b.tp = (float)br.tp;
+    b.c1 = (float)(va - xa * 0.5 * (ep - em));
+    b.ap = (float)(xa * 0.5 * ep);
+    b.am = (float)(xa * 0.5 * em);
+    b.lu = (float)log1p(e2u);
+    b.ep = (float)ep;
+    b.em = (float)em;
+    b.xch = (float)(xa * cosh(br.tp));
+    b.xsh = (float)(xa * sinh(br.tp));
+    b.e2u = (float)e2u;
+    b.shp = (float)sinh(br.tp);
+    b.n = p.bins;
+    s.G = br.G;
+    s.ar = (float)(br.tp * ((1.0 - e2u) / (1.0 + e2u)));
+    s.cr = (float)cosh(br.tp);
+    s.flags = (active ? kSlotActive : 0) | (edge ? kSlotEdge : 0) | (br.capped ? kSlotCapped : 0);
+    return s;
+}
+
 // Mixed path with the plain FP64 bracket: FP64 peak, offset and per-pair constants, FP32 bins.
-// D2 (L = 1 only): second derivatives from the shifted FP32 sums (sums2_f32).
+// D2 (L = 1 only): second derivatives from the shifted FP32 sums (sums2_f32).  Pairs per trip
+// and lanes as in kv_f64_kernel.
 template <int L, bool DERIV, bool D2 = false>
 __global__ void __launch_bounds__(kBlock) kv_mixed_kernel(KParams p)
 {
-    const int lane = threadIdx.x % L;
-    constexpr int G = 32 / L;
-    const int g = (threadIdx.x % 32) / L;
+    static_assert(!D2 || L == 1, "second derivatives run one pair per lane");
+    constexpr int Q = 32 / L;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / L, l = lane % L;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
-    for (int64_t base = warp * G; base < p.n; base += nwarps * G) {
-        const int64_t i = base + g;
-        const bool active = i < p.n;
-        double v = active ? (double)((const float*)p.v)[i] : 1.0;
-        double x = active ? (double)((const float*)p.x)[i] : 1.0;
-        double lk, dv, dx;
-        const bool edge = edge_pair(v, x, lk, dv, dx);
-        const double va = edge ? 1.0 : fabs(v);
-        const double xa = edge ? 1.0 : x;
-        BracketD br = bracket_call(va, xa, p.log_eps, p.max_iter);
-        const double ep = exp(br.tp), em = 1.0 / ep;
-        const double u = va * br.tp;
-        const double h = (br.t1 - br.t0) / p.bins;
-        BinsF b;
-        b.s0 = (float)(br.t0 - br.tp);
-        b.h = (float)h;
-        b.v = (float)va;
-        b.u = (float)u;
-        b.tp = (float)br.tp;
-        b.c1 = (float)(va - xa * 0.5 * (ep - em));
-        b.ap = (float)(xa * 0.5 * ep);
-        b.am = (float)(xa * 0.5 * em);
-        b.lu = (float)log1p(exp(-2.0 * u));
-        b.ep = (float)ep;
-        b.em = (float)em;
-        b.xch = (float)(xa * cosh(br.tp));
-        b.xsh = (float)(xa * sinh(br.tp));
-        b.n = p.bins;
-        if constexpr (D2) {
-            const double e2u = exp(-2.0 * u);
-            b.e2u = (float)e2u;
-            b.shp = (float)sinh(br.tp);
-            const Sums2<float> m = sums2_f32<L>(b, lane);
-            if (active) {
-                double d2v, dvx, d2x;
-                uint8_t st = KV_PAIR_OK;
-                if (edge) {
-                    edge_second(x, d2v, dvx, d2x);
-                    st = KV_PAIR_EDGE;
-                } else {
-                    float fdv, fdx, fd2v, fdvx, fd2x;
-                    moments_finish<float>(m, (float)(br.tp * ((1.0 - e2u) / (1.0 + e2u))), (float)cosh(br.tp),
-                                          fdv, fdx, fd2v, fdvx, fd2x);
-                    lk = br.G + (double)logf(b.h * m.s0);
-                    dv = v == 0.0 ? 0.0 : copysign((double)fdv, v);
-                    dx = fdx;
-                    d2v = fd2v;
-                    dvx = v == 0.0 ? 0.0 : copysign(1.0, v) * (double)fdvx;
-                    d2x = fd2x;
-                    if (br.capped) st = KV_PAIR_RANGE_CAP;
+    for (int64_t base = warp * Q; base < p.n; base += nwarps * Q) {
+        {
+            const int64_t i = base + g;
+            const SlotF s = bracket_slot_mixed<L>(p, i);
+            const bool active = s.flags & kSlotActive;
+            const bool edge = s.flags & kSlotEdge;
+            const uint8_t st = edge ? KV_PAIR_EDGE : (s.flags & kSlotCapped) ? KV_PAIR_RANGE_CAP : KV_PAIR_OK;
+            const double v = (double)s.vin;
+            double lk, dv, dx;
+            edge_pair(v, (double)s.xin, lk, dv, dx);
+            if constexpr (D2) {
+                const Sums2<float> m = sums2_f32<1>(s.b, 0);
+                if (active) {
+                    double d2v, dvx, d2x;
+                    if (edge) {
+                        edge_second((double)s.xin, d2v, dvx, d2x);
+                    } else {
+                        float fdv, fdx, fd2v, fdvx, fd2x;
+                        moments_finish<float>(m, s.ar, s.cr, fdv, fdx, fd2v, fdvx, fd2x);
+                        lk = s.G + (double)logf(s.b.h * m.s0);
+                        dv = v == 0.0 ? 0.0 : copysign((double)fdv, v);
+                        dx = fdx;
+                        d2v = fd2v;
+                        dvx = v == 0.0 ? 0.0 : copysign(1.0, v) * (double)fdvx;
+                        d2x = fd2x;
+                    }
+                    store_outputs<float>(p, i, lk, dv, dx, st);
+                    store_second<float>(p, i, d2v, dvx, d2x);
                 }
-                store_outputs<float>(p, i, lk, dv, dx, st);
-                store_second<float>(p, i, d2v, dvx, d2x);
-            }
-            continue;
-        }
-        float S0, S1, S2;
-        sums_f32<L, DERIV>(b, lane, S0, S1, S2);
-        if (active && lane == 0) {
-            uint8_t st = KV_PAIR_OK;
-            if (edge) {
-                st = KV_PAIR_EDGE;
             } else {
-                lk = br.G + (double)logf(b.h * S0);
-                float r = 1.0f / S0;
-                dv = DERIV ? copysign((double)(S1 * r), v) : 0.0;
-                if (v == 0.0) dv = 0.0;
-                dx = DERIV ? -(double)(S2 * r) : 0.0;
-                if (br.capped) st = KV_PAIR_RANGE_CAP;
+                float S0, S1, S2;
+                sums_f32<L, DERIV>(s.b, l, S0, S1, S2);
+                if (active && l == 0) {
+                    if (!edge) {
+                        lk = s.G + (double)logf(s.b.h * S0);
+                        float r = 1.0f / S0;
+                        dv = DERIV ? copysign((double)(S1 * r), v) : 0.0;
+                        if (v == 0.0) dv = 0.0;
+                        dx = DERIV ? -(double)(S2 * r) : 0.0;
+                    }
+                    store_outputs<float>(p, i, lk, dv, dx, st);
+                }
             }
-            store_outputs<float>(p, i, lk, dv, dx, st);
         }
     }
 }
@@ -373,7 +444,7 @@ __global__ void __launch_bounds__(kBlock) kv_bracket_kernel(const T* v, const T*
             if (gtp) gtp[i] = nan("");
             continue;
         }
-        BracketD br = bracket_call(vv, xx, log_eps, max_iter);
+        BracketD br = bracket_call(vv, xx, log_eps, max_iter, 0);
         if (t0) t0[i] = br.t0;
         if (tp) tp[i] = br.tp;
         if (t1) t1[i] = br.t1;
@@ -415,7 +486,9 @@ __global__ void kv_grad2_kernel(Grad2Args<T> a)
     }
 }
 
-// Deterministic two-stage sum: fixed grid for a given n, fixed reduction order.
+// Deterministic two-stage sum: fixed grid for a given n, fixed reduction order.  kv_noalloc.cu
+// repeats these two kernels for the sum without allocation (same order, same bits): a change
+// here must be made there too.
 constexpr int kSumBlock = 256;
 
 template <typename T>
@@ -452,24 +525,27 @@ __global__ void __launch_bounds__(kSumBlock) kv_sum_final(const double* part, in
 // ------------------------------------------------------------------ host side
 
 template <typename K>
-int resident_blocks(K kernel)
+int resident_blocks(K kernel, int block)
 {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kBlock, 0) != cudaSuccess || b < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, block, 0) != cudaSuccess || b < 1)
         b = 1;
+    cudaGetLastError();
     return b;
 }
 
 template <typename K>
-int launch_pairs(K kernel, const KParams& p, int lanes, cudaStream_t s)
+int launch_pairs(K kernel, const KParams& p, int pairs_per_warp, cudaStream_t s)
 {
-    // persistent grid: at most the resident blocks of every SM, at least enough for the pairs
-    int64_t threads = ((p.n * lanes + 31) / 32) * 32;
-    int64_t need = (threads + kBlock - 1) / kBlock;
-    int64_t cap = (int64_t)kvh::sm_count() * resident_blocks(kernel);
+    // persistent grid of at most the resident blocks of every SM; a block's four warps run on
+    // the SM's four sub-partitions
+    const int64_t warps = (p.n + pairs_per_warp - 1) / pairs_per_warp;
+    const int block = kBlock;
+    const int64_t need = (warps * 32 + block - 1) / block;
+    const int64_t cap = (int64_t)kvh::sm_count() * resident_blocks(kernel, block);
     int grid = (int)(need < cap ? need : cap);
     if (grid < 1) grid = 1;
-    kernel<<<grid, kBlock, 0, s>>>(p);
+    kernel<<<grid, block, 0, s>>>(p);
     KV_LAUNCH_CHECK();
     return KV_OK;
 }
@@ -477,26 +553,28 @@ int launch_pairs(K kernel, const KParams& p, int lanes, cudaStream_t s)
 // Second derivatives: one pair per thread.
 int dispatch_second(const KParams& p, int dtype, cudaStream_t s)
 {
-    if (dtype == KV_F64) return launch_pairs(kv_f64_kernel<1, true, true>, p, 1, s);
-    return launch_pairs(kv_mixed_kernel<1, true, true>, p, 1, s);
+    if (dtype == KV_F64) return launch_pairs(kv_f64_kernel<1, true, true>, p, 32, s);
+    return launch_pairs(kv_mixed_kernel<1, true, true>, p, 32, s);
 }
 
 template <int L>
 int dispatch_deriv(const KParams& p, int dtype, bool deriv, cudaStream_t s)
 {
     if (dtype == KV_F64)
-        return deriv ? launch_pairs(kv_f64_kernel<L, true>, p, L, s)
-                     : launch_pairs(kv_f64_kernel<L, false>, p, L, s);
-    return deriv ? launch_pairs(kv_mixed_kernel<L, true>, p, L, s)
-                 : launch_pairs(kv_mixed_kernel<L, false>, p, L, s);
+        return deriv ? launch_pairs(kv_f64_kernel<L, true>, p, 32 / L, s)
+                     : launch_pairs(kv_f64_kernel<L, false>, p, 32 / L, s);
+    return deriv ? launch_pairs(kv_mixed_kernel<L, true>, p, 32 / L, s)
+                 : launch_pairs(kv_mixed_kernel<L, false>, p, 32 / L, s);
 }
 
 int auto_lanes(int64_t n)
 {
-    // enough threads to fill every SM with about 1024 resident threads
-    int64_t want = (int64_t)kvh::sm_count() * 1024;
-    int L = 1;
-    while (L < 32 && n * L < want) L *= 2;
+    // the most lanes per pair (fewest pairs per warp) for which the batch still needs no more
+    // warps than the GPU has SM sub-partitions (four per SM): small batches then keep every
+    // sub-partition's FP64 unit busy, large ones run one pair per lane
+    const int64_t slots = 4 * (int64_t)kvh::sm_count();
+    int L = 32;
+    while (L > 1 && (n * L + 31) / 32 > slots) L /= 2;
     return L;
 }
 
@@ -520,6 +598,7 @@ int validate(const kv_args* a, int* bins, double* log_eps, int* max_iter, int* l
         return KV_ERR_ARG;
     if (a->bracket != KV_BRACKET_PLAIN && a->dtype != KV_MIXED) return KV_ERR_DTYPE;
     if (a->bracket == KV_BRACKET_MLP && !a->mlp) return KV_ERR_HANDLE;
+    if (a->flags & ~KV_FLAG_PEAK_ANALYTIC_START) return KV_ERR_ARG;
     size_t es = kvh::elem_size(a->dtype);
     const void* ptrs[9] = {a->v, a->x, a->logk, a->dv, a->dx, a->grad_out, a->d2v, a->dvx, a->d2x};
     for (const void* q : ptrs)
@@ -558,6 +637,7 @@ int kvh::fwd_bwd_ex(const kv_args* a, uint32_t* scratch)
     p.bins = bins;
     p.log_eps = log_eps;
     p.max_iter = max_iter;
+    p.flags = a->flags;
     const bool deriv = a->dv || a->dx;
     cudaStream_t s = (cudaStream_t)a->stream;
     if (a->d2v || a->dvx || a->d2x) return dispatch_second(p, a->dtype, s);

@@ -86,10 +86,12 @@ def kv_fwd_bwd(v, x, bins: int = 0):
 def kv_fwd_bwd_ex(v, x, *, bins: int = 0, bracket: str = "plain", log_eps: float = 0.0,
                   max_iter: int = 0, lanes: int = 0, mlp=None, grad_out=None,
                   want=("logk", "dv", "dx"), status: bool = False, fallback_count=None,
-                  out=None, second: bool = False):
+                  out=None, second: bool = False, analytic_peak_start: bool = False):
     """The general call (kv_fwd_bwd_ex).  Returns a dict with the requested outputs and, with
     ``status=True``, the per-pair status bytes; ``second=True`` adds the second derivatives
-    ``d2v``, ``dvx``, ``d2x`` (Sec. 4.1, n + m = 2).  ``out`` may supply preallocated tensors."""
+    ``d2v``, ``dvx``, ``d2x`` (Sec. 4.1, n + m = 2).  ``out`` may supply preallocated tensors.
+    ``analytic_peak_start=True`` sets KV_FLAG_PEAK_ANALYTIC_START (the FP64 bracket's peak search
+    on [0, asinh(v/x)] instead of Algorithm 1's doublings)."""
     v, x, dt = _check_pair(v, x)
     out = dict(out or {})
     want = tuple(want) + (("d2v", "dvx", "d2x") if second else ())
@@ -121,6 +123,7 @@ def kv_fwd_bwd_ex(v, x, *, bins: int = 0, bracket: str = "plain", log_eps: float
     a.stream = _stream_ptr(v.device)
     if second:
         a.d2v, a.dvx, a.d2x = (out[k].data_ptr() for k in ("d2v", "dvx", "d2x"))
+    a.flags = N.KV_FLAG_PEAK_ANALYTIC_START if analytic_peak_start else 0
     N.check(N.lib().kv_fwd_bwd_ex(ctypes.byref(a)), "kv_fwd_bwd_ex")
     return out
 

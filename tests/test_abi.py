@@ -117,3 +117,20 @@ def test_f32_bracket_argument_errors(lib):
     assert lib.kv_fwd_bwd_ex(ctypes.byref(a)) == -4  # FP64 I/O has no FP32 bracket
     a.bracket = 3
     assert lib.kv_fwd_bwd_ex(ctypes.byref(a)) == -7
+
+
+def test_flags_argument_errors(lib):
+    """kv_args.flags: unknown bits are rejected on the host, before any launch."""
+    a = N.KvArgs()
+    a.v = a.x = a.logk = 256
+    a.n, a.bins, a.dtype = 10, 32, 0
+    a.flags = 2
+    assert lib.kv_fwd_bwd_ex(ctypes.byref(a)) == -7
+    a.flags = -1
+    assert lib.kv_fwd_bwd_ex(ctypes.byref(a)) == -7
+    a.flags = N.KV_FLAG_PEAK_ANALYTIC_START
+    a.log_eps = 1.0  # the flag itself is valid: the next check (log_eps) reports
+    assert lib.kv_fwd_bwd_ex(ctypes.byref(a)) == -7
+    a.log_eps = 0.0
+    a.bins = -1
+    assert lib.kv_fwd_bwd_ex(ctypes.byref(a)) == -3

@@ -89,6 +89,44 @@ def test_lanes_per_pair(lanes):
     assert rel_logk(_np(outm["logk"]), ref32["logk"]).max() < TOL_MIXED
 
 
+def test_analytic_peak_start_flag():
+    """KV_FLAG_PEAK_ANALYTIC_START (the FP64 bracket's peak search on [0, asinh(v/x)] instead of
+    Algorithm 1's doublings): the FP64 path stays within 1e-13 of the oracle's method (which
+    follows Algorithms 1-3), the mixed path with the FP64 bracket within 2e-6, on the whole domain
+    and the hard band, including pairs with no peak (v^2 <= x) and edge inputs."""
+    v1, x1 = W.full_domain(3000, seed=231)
+    v2, x2 = W.hard_band(3000, seed=232)
+    v = np.concatenate([v1, v2, [0.0, 1.0, 1e-3, 1000.0, 50.0, -7.5, 2.0]])
+    x = np.concatenate([x1, x2, [1.0, 1.0, 1e-6, 1e-6, 1e5, 3.0, 4.0]])
+    ref = oracle.o1(v, x, bins=128, precision="long")
+    out = kv.kv_fwd_bwd_ex(_t(v), _t(x), bins=128, analytic_peak_start=True)
+    assert rel_logk(_np(out["logk"]), ref["logk"]).max() < TOL_F64
+    z = v == 0
+    assert np.all(_np(out["dv"])[z] == 0)
+    assert rel(_np(out["dv"])[~z], ref["dv"][~z]).max() < TOL_F64
+    assert rel(_np(out["dx"]), ref["dx"]).max() < TOL_F64
+    plain = kv.kv_fwd_bwd_ex(_t(v), _t(x), bins=128)
+    assert not torch.equal(plain["logk"], out["logk"])  # the flag reached the kernel
+    (vf, v32), (xf, x32) = W.to_f32(v, x)
+    ref32 = oracle.o1(v32, x32, bins=32, log_eps=MIXED_LOG_EPS, precision="long")
+    o32 = kv.kv_fwd_bwd_ex(_t(vf, torch.float32), _t(xf, torch.float32), bins=32, analytic_peak_start=True)
+    assert rel_logk(_np(o32["logk"]), ref32["logk"]).max() < TOL_MIXED
+    assert rel(_np(o32["dx"]), ref32["dx"]).max() < TOL_MIXED
+
+
+@pytest.mark.parametrize("n", [1, 31, 4096, 5000])
+def test_fp64_small_batches_every_lane_split(n):
+    """Small batches, where every lane brackets its own pair and groups of L lanes then share
+    the pairs' bins (constants by warp shuffles): all L give the oracle's results at 1e-13, and
+    a ragged last warp stores exactly its pairs."""
+    v, x = W.uniform_small(n, seed=233)
+    ref = oracle.o1(v, x, bins=128, precision="long")
+    for lanes in (1, 4, 32):
+        out = kv.kv_fwd_bwd_ex(_t(v), _t(x), bins=128, lanes=lanes)
+        assert rel_logk(_np(out["logk"]), ref["logk"]).max() < TOL_F64
+        assert rel(_np(out["dx"]), ref["dx"]).max() < TOL_F64
+
+
 def test_bracket_matches_oracle():
     """kv_bracket (Algorithms 1-3 on the GPU) against the oracle's bracket."""
     v, x = W.full_domain(3000, seed=205)
