@@ -9,10 +9,10 @@
 //    sign need only FP32 relative accuracy of the two terms);
 //  * the range searches work on h(t) = g(t) - g(t_r) - log eps through the cancellation-free
 //    difference of kv_bins.cuh about a reference point t_r next to the peak (the caller supplies
-//    the per-pair constants at t_r), so h is accurate to a few 1e-7 of its terms instead of
-//    losing |g| 2^-24 to the subtraction of two large numbers.  g(t_r) <= g(t_p) by at most a
-//    fraction of a nat (t_r is within ln2/256 of the FP32 peak), which widens the range by that
-//    much.
+//    the per-pair constants at t_r), in its coarse form (absolute error about 2^-22 of
+//    x e^{+-t_r}/2), instead of losing |g| 2^-24 to the subtraction of two large numbers.
+//    g(t_r) <= g(t_p) by at most a fraction of a nat (t_r is within ln2/256 of the FP32 peak),
+//    which widens the range by that much.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -47,18 +47,17 @@ __device__ __forceinline__ void eval_g1_g2_f32(float v, float x, float t, float&
     dF = v * v * (4.0f * e2 * r * r) - x * ch;
 }
 
-// F = h(t) = g(t_r + s) - g(t_r) - log eps with s = t - t_r, F' = g'(t) (the range searches).
+// F = h(t) = g(t_r + s) - g(t_r) - log eps with s = t - t_r, F' = g'(t) (the range searches),
+// from the coarse form of the same cancellation-free difference that the learned path's range
+// check uses (kv_bins.cuh delta_g_coarse: phi(+-s) = e^{+-s} - 1 -+ s from the approximate
+// exponential, no series).  Its error, about 2^-22 of x e^{+-t_r}/2 in absolute terms, moves the
+// range's ends by a vanishing fraction of a nat of the eps level; the searches need only the sign
+// of h and a usable slope.
 __device__ __forceinline__ void eval_h_f32(const BinsF& b, float le, float t, float& F, float& dF)
 {
-    const float s = t - b.tp;
-    float php, phm, es, ems;
-    phi_pair(s, php, phm, es, ems);
-    const float vt = fmaf(b.v, s, b.u);
-    const float e2 = ex2_approx(-2.0f * LOG2E_F * vt);
-    const float d = fmaf(lg2_approx(1.0f + e2), LN2_F, -b.lu);
-    F = (fmaf(b.c1, s, d) - fmaf(b.ap, php, b.am * phm)) - le;
-    // g'(t_r + s) = (v - x sinh t_r) - 2v e^{-2vt}/(1 + e^{-2vt}) - (x e^{t_r}/2)(e^s - 1) + (x e^{-t_r}/2)(e^{-s} - 1)
-    dF = b.c1 - 2.0f * b.v * e2 * rcp_approx(1.0f + e2) - b.ap * (es - 1.0f) + b.am * (ems - 1.0f);
+    float e2, es, ems;
+    F = delta_g_coarse(b, t - b.tp, e2, es, ems) - le;
+    dF = delta_g_slope_f32(b, e2, es, ems);
 }
 
 template <int KIND>
@@ -94,7 +93,11 @@ __device__ __forceinline__ bool find_range_f32(float v, float x, const BinsF& b,
     return F < 0.0f;
 }
 
-// Algorithm 2 in FP32 with a fixed trip count.
+// Algorithm 2 in FP32 with a fixed trip count.  Each iteration evaluates F at both the bisection
+// point and the Newton point and selects the update with predicates (the Newton point's value is
+// used only where the bisection point is on the positive side, as in the algorithm): lanes of a
+// warp that would take different sides of the test then run the same instructions instead of
+// running the two sides one after the other.
 template <int KIND>
 __device__ __forceinline__ float find_zero_f32(float v, float x, const BinsF& b, float le, float t_neg,
                                                float t_pos, float Fa, float dFa, int max_iter)
@@ -103,26 +106,17 @@ __device__ __forceinline__ float find_zero_f32(float v, float x, const BinsF& b,
     for (int i = 0; i < max_iter; ++i) {
         const float shrink = a + (bb - a) * 0.5f;
         float newton = a - __fdividef(Fa, dFa);
-        if (!isfinite(newton)) newton = shrink;
+        newton = isfinite(newton) ? newton : shrink;
         newton = fminf(fmaxf(newton, fminf(t_neg, shrink)), fmaxf(t_neg, shrink));
-        float Fs, dFs;
+        float Fs, dFs, Fn, dFn;
         eval_F_f32<KIND>(v, x, b, le, shrink, Fs, dFs);
-        if (Fs < 0.0f) {
-            a = shrink;
-            Fa = Fs;
-            dFa = dFs;
-        } else {
-            float Fn, dFn;
-            eval_F_f32<KIND>(v, x, b, le, newton, Fn, dFn);
-            if (Fn < 0.0f) {
-                a = newton;
-                bb = shrink;
-                Fa = Fn;
-                dFa = dFn;
-            } else {
-                bb = newton;
-            }
-        }
+        eval_F_f32<KIND>(v, x, b, le, newton, Fn, dFn);
+        const bool s_neg = Fs < 0.0f;           // the bisection point becomes the negative end
+        const bool n_neg = !s_neg && Fn < 0.0f;  // else the Newton point does, if negative
+        a = s_neg ? shrink : (n_neg ? newton : a);
+        Fa = s_neg ? Fs : (n_neg ? Fn : Fa);
+        dFa = s_neg ? dFs : (n_neg ? dFn : dFa);
+        bb = s_neg ? bb : (n_neg ? shrink : newton);
     }
     return a;
 }
