@@ -166,7 +166,24 @@ template <int STEPS = 2>
 __device__ __forceinline__ float peak_f32(float v, float x)
 {
     if (!(v * v > x)) return 0.0f;
-    float t = fast_asinh(__fdividef(v, x)) * (1.0f + 0x1.0p-16f);
+    const float q = __fdividef(v, x);
+    const float a = fast_asinh(q);
+    float t = a;
+    // Where v a >= 1 both other bounds lie at or above a (at t = a, v^2 t / x >= q = sinh t), so
+    // they are computed only where v a < 1 (each lane by its own test, so a pair's result does
+    // not depend on the other pairs of its warp).
+    if (v * a < 1.0f) {
+        const float f = fast_asinh(fminf(q, v * q * a));
+        const float d = fmaf(v, v, -x) * rcp_approx(30.0f * x);  // (r - 1)/30, v^2 - x rounded once
+        const float e = d + 1.0f / 36.0f;
+        float rs;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(e));
+        const float z = 60.0f * d * rcp_approx(fmaf(e, rs, 1.0f / 6.0f));
+        float rz;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rz) : "f"(z));
+        t = fminf(fminf(a, f), z * rz);
+    }
+    t *= 1.0f + 0x1.0p-16f;
 #pragma unroll
     for (int k = 0; k < STEPS; ++k) {
         float e2 = ex2_approx(-2.0f * LOG2E_F * v * t);
@@ -533,11 +550,12 @@ constexpr uint32_t kTmemCols = 64;
 // the FP32 plain-bracket path.  A regular pair whose range failed goes to the fallback list and
 // runs the bins on a placeholder range (results discarded), so that every lane of the warp runs
 // the same straight-line code into the bins.  Then FP32 bins, the finish with the float-float
-// offset, and the stores.
+// offset, and the stores.  An edge pair's results are taken from (v, x) again after the bins, so
+// that they hold no registers during them.
 template <bool DERIV, bool D2>
 __device__ __forceinline__ void pair_tail(const MlpPathParams& p, int64_t i, bool active, bool edge, bool ok,
-                                          float v, float x, PeakConst& c, float t0, float t1, float lk,
-                                          float dv, float dx, uint8_t ok_status = KV_PAIR_OK)
+                                          float v, float x, PeakConst& c, float t0, float t1,
+                                          uint8_t ok_status = KV_PAIR_OK)
 {
     const float tr = c.b.tp;
     const bool regular = active && !edge;
@@ -571,6 +589,8 @@ __device__ __forceinline__ void pair_tail(const MlpPathParams& p, int64_t i, boo
     } else {
         sums_f32<1, DERIV, true>(c.b, 0, S0, S1, S2);
     }
+    float lk, dv, dx;
+    float_edge(v, x, lk, dv, dx);
     if (regular && ok) {
         // log(h S0) from the approximate log2 (absolute error about 1e-7)
         df L = df_add(c.G, df_make(lg2_approx(c.b.h * S0) * LN2_F));
@@ -618,8 +638,7 @@ __global__ void __launch_bounds__(kMlpBlock) kv_plain_f32_kernel(MlpPathParams p
         PeakConst c = peak_constants(va, xa, tp, g_exp_tab);
         float t0, t1;
         const bool ok = range_alg12_f32(c.b, tp, p.log_eps, max_iter, t0, t1, capped);
-        pair_tail<DERIV, D2>(p, i, active, edge, ok, v, x, c, t0, t1, lk, dv, dx,
-                             capped ? KV_PAIR_RANGE_CAP : KV_PAIR_OK);
+        pair_tail<DERIV, D2>(p, i, active, edge, ok, v, x, c, t0, t1, capped ? KV_PAIR_RANGE_CAP : KV_PAIR_OK);
     }
 }
 
@@ -745,7 +764,7 @@ __global__ void __launch_bounds__(kMlpBlock, D2 ? 6 : 8) kv_mlp_tc_kernel(MlpPat
         const float w1 = fmaxf(fmaxf(__expf(L1) - DELTA, 0.0f) + (tp - tr), 1e-6f * (1.0f + tr));
         float t0, t1;
         const bool ok = check_range(c.b, tr, w0, w1, p.log_eps, lo_ok, t0, t1);
-        pair_tail<DERIV, D2>(p, i, active, edge, ok, v, x, c, t0, t1, lk, dv, dx);
+        pair_tail<DERIV, D2>(p, i, active, edge, ok, v, x, c, t0, t1);
     }
     if (aborted) {
         // a tensor-core wait ran out: the remaining pairs of this CTA go to the fallback pass
@@ -803,6 +822,7 @@ struct FallbackParams {
     MlpPathParams p;
     double log_eps;
     int max_iter;
+    int flags;    // kv_args.flags (the FP64 bracket's peak start)
     int try_f32;  // first try the plain bracket in FP32 (the learned path's failures)
     unsigned long long* fallback_total;
 };
@@ -893,7 +913,7 @@ __global__ void __launch_bounds__(kMlpBlock) kv_fallback_kernel(FallbackParams f
         }
         const double v = (double)p.v[i], x = (double)p.x[i];
         const double va = fabs(v);
-        BracketD br = bracket_f64(va, x, f.log_eps, f.max_iter);
+        BracketD br = bracket_f64(va, x, f.log_eps, f.max_iter, (f.flags & KV_FLAG_PEAK_ANALYTIC_START) != 0);
         const double ep = exp(br.tp), em = 1.0 / ep;
         const double u = va * br.tp;
         const double h = (br.t1 - br.t0) / p.bins;
@@ -1272,6 +1292,7 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
         f.p = p;
         f.log_eps = log_eps;
         f.max_iter = max_iter;
+        f.flags = a->flags;
         f.try_f32 = f32_plain ? 0 : 1;
         f.fallback_total = a->fallback_count;
         int grid = sm_count();  // grid-stride over the list; most calls have none

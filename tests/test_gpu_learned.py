@@ -3,7 +3,6 @@ fast path (MLP bracket, float-float offset, FP32 bins, plain fallback) against t
 """
 import os
 import tempfile
-import time
 
 import numpy as np
 import pytest
@@ -318,23 +317,38 @@ def test_mlp_path_full_size_sampled(net):
 
 
 def test_learned_bracket_gain(net):
-    """What the trained network gains: the fast path against the same mixed path with the plain
-    FP64 bracket on the same 4M pairs (and the same accuracy bar, checked above)."""
+    """What the trained network gains over the method without it, on the same 4M hard-band pairs
+    at 32 bins and the same accuracy bar: against the mixed path with the paper's FP64 bracket,
+    and against the fastest form of the method without a network, Algorithms 1-3 in FP32 with the
+    same offset, bins and finish (KV_BRACKET_PLAIN_F32).  Both brackets' results are checked
+    against the oracle on a sample here as well, so the times compare equal accuracy."""
     n = 1 << 22
     v, x = W.hard_band(n, seed=314)
-    vt, xt = _t(v, torch.float32), _t(x, torch.float32)
+    (vf, v64), (xf, x64) = W.to_f32(v, x)
+    vt, xt = _t(vf, torch.float32), _t(xf, torch.float32)
 
     def timed(**kw):
+        out = kv.kv_fwd_bwd_ex(vt, xt, bins=32, **kw)
         for _ in range(2):
-            kv.kv_fwd_bwd_ex(vt, xt, bins=32, **kw)
+            kv.kv_fwd_bwd_ex(vt, xt, bins=32, out=out, **kw)
         torch.cuda.synchronize()
-        t = time.perf_counter()
-        for _ in range(3):
-            kv.kv_fwd_bwd_ex(vt, xt, bins=32, **kw)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(5):
+            kv.kv_fwd_bwd_ex(vt, xt, bins=32, out=out, **kw)
+        ev[1].record()
         torch.cuda.synchronize()
-        return (time.perf_counter() - t) / 3
+        return ev[0].elapsed_time(ev[1]) / 5e3, out
 
-    t_plain = timed(bracket="plain")
-    t_mlp = timed(bracket="mlp", mlp=net)
-    print(f"plain bracket {n / t_plain:.3e} pairs/s, learned bracket {n / t_mlp:.3e} pairs/s")
+    t_plain, _ = timed(bracket="plain")
+    t_f32, o_f32 = timed(bracket="f32")
+    t_mlp, o_mlp = timed(bracket="mlp", mlp=net)
+    idx = np.random.default_rng(315).choice(n, 2048, replace=False)
+    ref = oracle.o1(v64[idx], x64[idx], bins=32, log_eps=LOG_EPS, precision="long")
+    for o in (o_f32, o_mlp):
+        assert rel_logk(_np(o["logk"])[idx], ref["logk"]).max() < TOL
+        assert rel(_np(o["dx"])[idx], ref["dx"]).max() < TOL
+    print(f"FP64 bracket {n / t_plain:.3e} pairs/s, FP32 bracket {n / t_f32:.3e} pairs/s, "
+          f"learned bracket {n / t_mlp:.3e} pairs/s ({t_f32 / t_mlp:.2f}x the FP32 bracket)")
     assert t_mlp < 0.5 * t_plain
+    assert t_mlp * 1.5 < t_f32
