@@ -10,8 +10,10 @@ After the timed steps (outside the timed region) the outputs of the last timed s
 on a seeded sample against the oracle's fixed-bin method in long double at the same bins and eps;
 the line carries the errors and the run exits non-zero if any exceeds the accuracy bound.  The
 default run also times, each with its own accuracy sample: the learned path at 64 and 128 bins,
-the plain FP32 bracket at the headline's bins (the method without the network at its fastest) and
-the FP64 path at 128 bins on a slice of the same workload.
+the plain FP32 bracket at the headline's bins (the method without the network at its fastest),
+the FP64 path at 128 bins on a slice of the same workload, and the other workload configurations
+(`configs`: 4096 uniform-small pairs on the FP64 path, the 8M-sample GH log-likelihood through
+autograd, 64M learned-bracket evaluation pairs, 128M extreme-range pairs at 64 and 256 bins).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--bins 32]
     python bench.py --path learned|plain|f32|second|f64 [--workload hard_band|uniform_small]
@@ -73,26 +75,28 @@ F64_SLICE = 1 << 23     # the FP64 path's slice of the workload (134 MB of float
 #             is not counted), peak Newton, offset constants, endpoint check, setup and finish
 #             ~250                                                              -> 505
 # ncu's executed FFMA + FADD + FMUL (+ 2 x FFMA2/FADD2/FMUL2) counters over 4M hard-band pairs at
-# 1 and 32 bins (one launch of the fast-path kernel each) give 35.92 per bin and 505.1 per pair.
+# 1 and 32 bins (one launch of the fast-path kernel each) give 35.92 per bin and 505.15 per pair.
 FP32_OPS_PER_BIN = 35.92
 MUFU_OPS_PER_BIN = 4
-FP32_OPS_PER_PAIR = 505.1
+FP32_OPS_PER_PAIR = 505.15
 # XU-pipe (MUFU) operations per pair outside the bins from the same captures
-# (smsp__inst_executed_pipe_xu: 46.5 per pair at 1 bin, 4.0 per bin), and the XU pipe's lanes per
-# SM per clock that ncu's XU percentages are taken against (170.5 operations per pair in 0.330 ms
-# per 4M pairs read as 23.3 % there).
-MUFU_OPS_PER_PAIR = 38.5
+# (smsp__inst_executed_pipe_xu x 32: 47.2 per pair at 1 bin, 4.0 per bin), and the XU pipe's lanes
+# per SM per clock that ncu's XU percentages are taken against (171.2 operations per pair in
+# 0.331 ms per 4M pairs read as 23.2 percent there).
+MUFU_OPS_PER_PAIR = 39.2
 XU_LANES_PER_SM = 32
-# DRAM bytes per pair of the fast-path kernel from an ncu capture of one launch (read + write),
-# or None until one is taken for the current kernel.  The algorithmic bytes per pair are
-# v, x, grad_out in and log K, d/dv, d/dx out, 4 bytes each.
-TRAFFIC_BYTES_PER_PAIR = None
+# DRAM bytes per pair of the fast-path kernel (read + write) from an ncu capture of one full
+# 16,777,216-pair launch in steady state (the fourth of consecutive launches, no cache flush
+# between them, so the previous launch's outputs are written back inside it): 202.28 MB read +
+# 199.83 MB written.  The algorithmic bytes per pair are v, x, grad_out in and log K, d/dv, d/dx
+# out, 4 bytes each (402.65 MB per launch).
+TRAFFIC_BYTES_PER_PAIR = (202.28e6 + 199.83e6) / 16777216
 ALGORITHMIC_BYTES_PER_PAIR = 24
 # The counts above hold for the fast-path kernel built from these sources; COUNTS_SOURCE_SHA is
 # their hash when the counts were taken.  When the sources change, the line says so and reports
 # no traffic until the counters are taken again.
-COUNTS_SOURCES = ("kv_mlp.cu", "kv_bins.cuh", "kv_dfloat.cuh", "kv_bracket_f32.cuh")
-COUNTS_SOURCE_SHA = "e68e9b9e5c42eab8"
+COUNTS_SOURCES = ("kv_mlp.cu", "kv_bins.cuh", "kv_dfloat.cuh")
+COUNTS_SOURCE_SHA = "5c7a7caf8d016cce"
 
 PATHS = {
     # name: (bracket, second derivatives, float64 I/O)
@@ -403,6 +407,118 @@ def extra_entries(args, kv, mlp, vf, xf, v64c, x64c, dev, stream, sms, sm_mhz, p
     return res
 
 
+def config_entries(args, kv, mlp, dev, stream, check):
+    """The other workload configurations, each timed with CUDA events and checked on a sample:
+    uniform_small (4096 pairs, FP64, 128 bins, log K only), the GH log-likelihood through
+    autograd (8M float32 samples, forward with fused derivatives, deterministic sum, backward
+    epilogue), the learned-bracket evaluation (64M fresh pairs, network trained on 1M plain
+    brackets of the same distribution) and the extreme range (128M pairs at 64 and 256 bins, its
+    own network, against the FP64 path on a 2M slice)."""
+    import torch
+
+    from paper_2108_11560_gb300 import learned
+
+    res = {}
+    reps = max(3, args.steps // 2)
+    # uniform_small: 4096 pairs, FP64, log K only (kv_log)
+    v, x = W.uniform_small(4096, seed=0)
+    vt, xt = torch.from_numpy(v).to(dev), torch.from_numpy(x).to(dev)
+    out = torch.empty_like(vt)
+    total, _ = timed_steps(lambda: kv.kv_fwd_bwd_ex(vt, xt, bins=128, want=("logk",), out={"logk": out}),
+                           reps * 4, args.warmup, stream)
+    ms = total / (reps * 4)
+    e = {"pairs": 4096, "bins": 128, "value": 4096 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+         "path": "FP64, log K only"}
+    if check:
+        import oracle
+        ref = oracle.o1(v, x, bins=128, precision="long")["logk"]
+        g = out.double().cpu().numpy()
+        e["accuracy"] = {"max_rel_logk": float((np.abs(g - ref) / np.maximum(1.0, np.abs(ref))).max()),
+                         "pairs": 4096, "bound": TOL_F64}
+        e["accuracy"]["ok"] = e["accuracy"]["max_rel_logk"] <= TOL_F64
+    res["uniform_small_4096"] = e
+    # GH log-likelihood through autograd
+    n = 8_388_608
+    lam, xg, *_ = W.gh_likelihood(n, seed=2)
+    lt = torch.from_numpy(lam).to(dev).requires_grad_(True)
+    xt = torch.from_numpy(xg).to(dev).requires_grad_(True)
+    loss = [None]
+
+    def gh_step():
+        lt.grad = None
+        xt.grad = None
+        lk = kv.log_besselk(lt, xt, bins=40, bracket="mlp", mlp=mlp)
+        loss[0] = kv.kv_sum(lk.detach())
+        lk.backward(torch.ones_like(lk))
+    total, _ = timed_steps(gh_step, reps, args.warmup, stream)
+    ms = total / reps
+    e = {"pairs": n, "bins": 40, "value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+         "path": "learned bracket through torch.autograd: forward with fused derivatives, "
+                 "deterministic sum, backward epilogue"}
+    if check:
+        idx = sample_indices(n, ACC_SAMPLE_F64, 3000)
+        outs = {"logk": kv.log_besselk(lt.detach(), xt.detach(), bins=40, bracket="mlp", mlp=mlp),
+                "dv": lt.grad, "dx": xt.grad}
+        e["accuracy"] = accuracy(outs, lam.astype(np.float64), xg.astype(np.float64), idx, 40,
+                                 MIXED_LOG_EPS, TOL_MIXED)
+        e["loglik"] = float(loss[0].item())
+    res["gh_likelihood_8M"] = e
+    del lt, xt
+    # learned-bracket evaluation: 64M fresh pairs, a network trained on 1M plain brackets
+    net4, _ = learned.train_network(dev, domain="uniform")
+    n = 64 * 1024 * 1024
+    v, x = W.learned_bracket(n, seed=6)
+    vf, xf = v.astype(np.float32), x.astype(np.float32)
+    del v, x
+    vt, xt = torch.from_numpy(vf).to(dev), torch.from_numpy(xf).to(dev)
+    o = kv.kv_fwd_bwd_ex(vt, xt, bins=40, bracket="mlp", mlp=net4)
+    total, _ = timed_steps(lambda: kv.kv_fwd_bwd_ex(vt, xt, bins=40, bracket="mlp", mlp=net4, out=o), reps,
+                           args.warmup, stream)
+    ms = total / reps
+    e = {"pairs": n, "bins": 40, "value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+         "network": "trained on 1M plain brackets, v ~ U[0, 200], x log-uniform in [1e-4, 1e4]"}
+    if check:
+        fb, rate = fallback_pairs(kv, vt, xt, dict(bins=40, bracket="mlp", mlp=net4))
+        e["fallback_rate"] = rate
+        idx = sample_indices(n, ACC_SAMPLE_F64, 4000, fb)
+        e["accuracy"] = accuracy(o, vf.astype(np.float64), xf.astype(np.float64), idx, 40, MIXED_LOG_EPS,
+                                 TOL_MIXED)
+    res["learned_bracket_eval_64M"] = e
+    del vt, xt, o, vf, xf
+    # extreme range: 128M pairs, its own network; the FP64 path on a 2M slice
+    net5, _ = learned.train_network(dev, domain="extreme", seed=4)
+    n = 128 * 1024 * 1024
+    v, x = W.extreme_range(n, seed=5)
+    vf, xf = v.astype(np.float32), x.astype(np.float32)
+    del v, x
+    vt, xt = torch.from_numpy(vf).to(dev), torch.from_numpy(xf).to(dev)
+    m = 1 << 21
+    v64, x64 = vf[:m].astype(np.float64), xf[:m].astype(np.float64)
+    v64t, x64t = torch.from_numpy(v64).to(dev), torch.from_numpy(x64).to(dev)
+    for bins in (64, 256):
+        o = kv.kv_fwd_bwd_ex(vt, xt, bins=bins, bracket="mlp", mlp=net5)
+        total, _ = timed_steps(lambda: kv.kv_fwd_bwd_ex(vt, xt, bins=bins, bracket="mlp", mlp=net5, out=o),
+                               max(2, reps // 2), args.warmup, stream)
+        ms = total / max(2, reps // 2)
+        o64 = kv.kv_fwd_bwd_ex(v64t, x64t, bins=bins)
+        t64, _ = timed_steps(lambda: kv.kv_fwd_bwd_ex(v64t, x64t, bins=bins, out=o64), 2, 3, stream)
+        e = {"pairs": n, "bins": bins, "value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+             "network": "trained on 1M plain brackets of the extreme range",
+             "fp64_plain": {"pairs": m, "value": m / (t64 / 2 / 1e3), "unit": UNIT,
+                            "slice": f"first {m} pairs, float64 I/O"}}
+        if check:
+            fb, rate = fallback_pairs(kv, vt, xt, dict(bins=bins, bracket="mlp", mlp=net5))
+            e["fallback_rate"] = rate
+            idx = sample_indices(n, ACC_SAMPLE_F64, 5000 + bins, fb)
+            e["accuracy"] = accuracy(o, vf.astype(np.float64), xf.astype(np.float64), idx, bins,
+                                     MIXED_LOG_EPS, TOL_MIXED)
+            k = sample_indices(m, 1024, 6000 + bins)
+            e["fp64_plain"]["accuracy"] = accuracy(o64, v64, x64, k, bins, F64_LOG_EPS, TOL_F64)
+        res[f"extreme_range_128M_{bins}"] = e
+        del o, o64
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -570,6 +686,7 @@ def main():
             line["learned_vs_f32_bracket"] = value / world / line["f32_bracket"]["value"]
         if line["fp64_plain"]:
             line["learned_vs_fp64_plain"] = value / world / line["fp64_plain"]["value"]
+        line["configs"] = config_entries(args, kv, mlp, dev, stream, check)
     if world == 1 and not args.no_cpu_baseline and not f64io:
         line["cpu_baseline"] = cpu_baseline(v64c, x64c, args.bins)
     print(json.dumps(line), flush=True)
@@ -577,6 +694,8 @@ def main():
         dist.destroy_process_group()
     oks = [line["accuracy"]] + [e.get("accuracy") for e in line.get("sweep", {}).values()]
     oks += [(line.get(k) or {}).get("accuracy") for k in ("f32_bracket", "fp64_plain")]
+    for e in (line.get("configs") or {}).values():
+        oks += [e.get("accuracy"), (e.get("fp64_plain") or {}).get("accuracy")]
     if any(a is not None and not a["ok"] for a in oks):
         print("accuracy bound exceeded", file=sys.stderr)
         return 3
