@@ -293,7 +293,9 @@ def accuracy(outs, v64, x64, idx, bins, log_eps, bound, grad_out=None):
     e_x = np.abs(g["dx"] - ref["dx"]) / np.maximum(np.abs(ref["dx"]), 1e-300)
     worst = max(float(e_l.max()), float(e_v.max()), float(e_x.max()))
     return {"max_rel_logk": float(e_l.max()), "max_rel_dv": float(e_v.max()),
-            "max_rel_dx": float(e_x.max()), "pairs": int(idx.size), "bound": bound,
+            "max_rel_dx": float(e_x.max()),
+            "max_abs_logk": float(np.abs(g["logk"] - ref["logk"]).max()),  # = relative error of K
+            "pairs": int(idx.size), "bound": bound,
             "ok": bool(worst <= bound),
             "reference": f"oracle O1 in long double, {bins} bins, log eps {log_eps:.4g}",
             "oracle_s": round(secs, 2)}
