@@ -74,29 +74,34 @@ F64_SLICE = 1 << 23     # the FP64 path's slice of the workload (134 MB of float
 #   per pair: layer 1 and layer 3 on the CUDA cores 256 (layer 2 runs on the tensor cores and
 #             is not counted), peak Newton, offset constants, endpoint check, setup and finish
 #             ~250                                                              -> 505
-# ncu's executed FFMA + FADD + FMUL (+ 2 x FFMA2/FADD2/FMUL2) counters over 4M hard-band pairs at
-# 1 and 32 bins (one launch of the fast-path kernel each) give 35.92 per bin and 505.15 per pair.
-FP32_OPS_PER_BIN = 35.92
+# ncu's executed FFMA + FADD + FMUL (+ 2 x FFMA2/FADD2/FMUL2) counters over 4M hard-band pairs (one
+# launch of the fast-path kernel each) give these per bin and per pair: for the kernel instance
+# with plain block sums (up to PLAIN_SUMS_MAX_BINS bins), from launches at 1 and 32 bins; for the
+# instance with compensated block sums (more bins), from launches at 41 and 64 bins.
+PLAIN_SUMS_MAX_BINS = 40
+FP32_OPS_PER_BIN = 33.886
+FP32_OPS_PER_PAIR = 488.22
+FP32_OPS_PER_BIN_COMP = 35.703
+FP32_OPS_PER_PAIR_COMP = 518.20
 MUFU_OPS_PER_BIN = 4
-FP32_OPS_PER_PAIR = 505.15
 # XU-pipe (MUFU) operations per pair outside the bins from the same captures
 # (smsp__inst_executed_pipe_xu x 32: 47.2 per pair at 1 bin, 4.0 per bin), and the XU pipe's lanes
 # per SM per clock that ncu's XU percentages are taken against (171.2 operations per pair in
-# 0.331 ms per 4M pairs read as 23.2 percent there).
+# 0.320 ms per 4M pairs read as 24 percent there).
 MUFU_OPS_PER_PAIR = 39.2
 XU_LANES_PER_SM = 32
 # DRAM bytes per pair of the fast-path kernel (read + write) from an ncu capture of one full
-# 16,777,216-pair launch in steady state (the fourth of consecutive launches, no cache flush
-# between them, so the previous launch's outputs are written back inside it): 202.28 MB read +
-# 199.83 MB written.  The algorithmic bytes per pair are v, x, grad_out in and log K, d/dv, d/dx
-# out, 4 bytes each (402.65 MB per launch).
-TRAFFIC_BYTES_PER_PAIR = (202.28e6 + 199.83e6) / 16777216
+# 16,777,216-pair launch at 32 bins in steady state (the fourth of five consecutive launches, no
+# cache flush between them, so the previous launch's outputs are written back inside it):
+# 201.38 MB read + 199.85 MB written.  The algorithmic bytes per pair are v, x, grad_out in and
+# log K, d/dv, d/dx out, 4 bytes each (402.65 MB per launch).
+TRAFFIC_BYTES_PER_PAIR = (201.38e6 + 199.85e6) / 16777216
 ALGORITHMIC_BYTES_PER_PAIR = 24
 # The counts above hold for the fast-path kernel built from these sources; COUNTS_SOURCE_SHA is
 # their hash when the counts were taken.  When the sources change, the line says so and reports
 # no traffic until the counters are taken again.
 COUNTS_SOURCES = ("kv_mlp.cu", "kv_bins.cuh", "kv_dfloat.cuh")
-COUNTS_SOURCE_SHA = "5c7a7caf8d016cce"
+COUNTS_SOURCE_SHA = "a6ba49e6ccc71c00"
 
 PATHS = {
     # name: (bracket, second derivatives, float64 I/O)
@@ -244,10 +249,17 @@ def sfu_utilisation(n_pairs, bins, launch_ms, sms, sm_mhz):
                            f"ncu's pipe percentages use)"}
 
 
+def fp32_ops(bins):
+    """FP32 operations per pair of the fast-path kernel instance that runs at this bin count."""
+    if bins <= PLAIN_SUMS_MAX_BINS:
+        return FP32_OPS_PER_PAIR + (bins + 1) * FP32_OPS_PER_BIN
+    return FP32_OPS_PER_PAIR_COMP + (bins + 1) * FP32_OPS_PER_BIN_COMP
+
+
 def fp32_roofline(n_pairs, bins, launch_ms, sms, sm_mhz, peak_src):
     """Algorithmic FP32 operations of the fast-path kernel per launch over its launch time,
     against the FP32 pipe's peak (128 lanes per SM per clock, an FMA counted as one operation)."""
-    ops = n_pairs * (FP32_OPS_PER_PAIR + (bins + 1) * FP32_OPS_PER_BIN)
+    ops = n_pairs * fp32_ops(bins)
     achieved = ops / (launch_ms / 1e3)
     peak = sms * 128 * sm_mhz * 1e6
     return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,

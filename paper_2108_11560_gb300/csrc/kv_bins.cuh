@@ -421,47 +421,65 @@ __device__ __forceinline__ void bin_f32x2(const BinsF& b, const BinsK& k, float2
     }
 }
 
-// The three sums over bins m = lane, lane + L, ... <= n, compensated per block of four bins: a
-// block's four terms are added pairwise (two rounding levels) and the block sum goes into a Kahan
-// sum, so the relative error stays a few units of 2^-24 for any bin count at 1.75 additions per
-// term instead of Kahan's four.  The end weight 1/2 of bin 0 is applied to the first block's
-// first term (lane 0 only); bin n always falls in the tail loop, which selects its weight.
-// VOTE requires L = 1 and all 32 lanes of the warp in the call with the same n.
-template <int L, bool DERIV, bool VOTE = false>
+// The three sums over bins m = lane, lane + L, ... <= n: each block of four bins is added
+// pairwise (two rounding levels); the block sums are compensated (Kahan, COMP), so that the
+// relative error stays a few units of 2^-24 for any bin count at 1.75 additions per term, or added
+// plainly (!COMP: 1 addition per term), which for all-positive terms bounds the relative error by
+// (2 + k) units of 2^-24 after k sequential additions — at most 13 units for up to 40 bins per
+// lane (10 blocks and one tail bin), 7.7e-7, so that a ratio of two sums stays within 1.6e-6.
+// The end weight 1/2 of bin 0 is applied to the first block's first term (lane 0 only); bin n
+// always falls in the tail loop, which selects its weight.  VOTE requires L = 1 and all 32 lanes
+// of the warp in the call with the same n.
+constexpr int kPlainSumsMaxBins = 40;
+
+template <int L, bool DERIV, bool VOTE = false, bool COMP = true>
 __device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, float& S1, float& S2)
 {
-    static_assert(!VOTE || L == 1, "the warp vote needs every lane on the same bins");
     const BinsK k = bins_k(b);
     KahanSum<float> k0, k1, k2;
     k0.init();
     k1.init();
     k2.init();
+    float q0 = 0.0f, q1 = 0.0f, q2 = 0.0f;  // plain block sums (COMP = false)
     int m = lane;
     float mf = (float)lane;
     float c_first = lane == 0 ? 0.5f * k.kc : k.kc;
     for (; m + 3 * L < b.n; m += 4 * L, mf += (float)(4 * L)) {
-        // bins m, m + L in one float2 and m + 2L, m + 3L in another; the block's four terms are
-        // added pairwise, (w_m + w_{m+2L}) + (w_{m+L} + w_{m+3L}), and the sum goes to Kahan
         float2 wa, w1a, w2a, wb, w1b, w2b;
         bin_f32x2<DERIV, VOTE>(b, k, make_float2(mf, mf + (float)L), make_float2(c_first, k.kc), wa, w1a, w2a);
         bin_f32x2<DERIV, VOTE>(b, k, make_float2(mf + (float)(2 * L), mf + (float)(3 * L)), f2(k.kc), wb, w1b, w2b);
         c_first = k.kc;
         const float2 p0 = add2(wa, wb);
-        k0.add(p0.x + p0.y);
+        if (COMP) k0.add(p0.x + p0.y); else q0 += p0.x + p0.y;
         if (DERIV) {
             const float2 p1 = add2(w1a, w1b), p2 = add2(w2a, w2b);
-            k1.add(p1.x + p1.y);
-            k2.add(p2.x + p2.y);
+            if (COMP) {
+                k1.add(p1.x + p1.y);
+                k2.add(p2.x + p2.y);
+            } else {
+                q1 += p1.x + p1.y;
+                q2 += p2.x + p2.y;
+            }
         }
     }
     for (; m <= b.n; m += L, mf += (float)L) {
         float w, w1, w2;
         bin_f32<DERIV, VOTE>(b, k, mf, (m == 0 || m == b.n) ? 0.5f * k.kc : k.kc, w, w1, w2);
-        k0.add(w);
+        if (COMP) k0.add(w); else q0 += w;
         if (DERIV) {
-            k1.add(w1);
-            k2.add(w2);
+            if (COMP) {
+                k1.add(w1);
+                k2.add(w2);
+            } else {
+                q1 += w1;
+                q2 += w2;
+            }
         }
+    }
+    if (!COMP) {
+        k0.s = q0;
+        k1.s = q1;
+        k2.s = q2;
     }
     S0 = lane_sum<float, L>(k0.value());
     S1 = DERIV ? lane_sum<float, L>(k1.value()) : 0.0f;

@@ -552,7 +552,7 @@ constexpr uint32_t kTmemCols = 64;
 // the same straight-line code into the bins.  Then FP32 bins, the finish with the float-float
 // offset, and the stores.  An edge pair's results are taken from (v, x) again after the bins, so
 // that they hold no registers during them.
-template <bool DERIV, bool D2>
+template <bool DERIV, bool D2, bool COMP = true>
 __device__ __forceinline__ void pair_tail(const MlpPathParams& p, int64_t i, bool active, bool edge, bool ok,
                                           float v, float x, PeakConst& c, float t0, float t1,
                                           uint8_t ok_status = KV_PAIR_OK)
@@ -587,7 +587,7 @@ __device__ __forceinline__ void pair_tail(const MlpPathParams& p, int64_t i, boo
         if (v < 0.0f) dvx = -dvx;
         if (edge) d2v = dvx = d2x = (isinf(x) && x > 0.0f) ? 0.0f : nanf("");
     } else {
-        sums_f32<1, DERIV, true>(c.b, 0, S0, S1, S2);
+        sums_f32<1, DERIV, true, COMP>(c.b, 0, S0, S1, S2);
     }
     float lk, dv, dx;
     float_edge(v, x, lk, dv, dx);
@@ -619,8 +619,9 @@ __device__ __forceinline__ void pair_tail(const MlpPathParams& p, int64_t i, boo
 
 // The plain bracket in FP32 (Algorithms 1-3, kv_bracket_f32.cuh) followed by the fast path's
 // offset at a grid point, bins and finish: the paper's 32-bit variant of the whole path, one pair
-// per thread.  Pairs whose FP32 range is not a finite range go to the FP64 fallback.
-template <bool DERIV, bool D2 = false>
+// per thread.  Pairs whose FP32 range is not a finite range go to the FP64 fallback.  COMP: the
+// bins' block sums compensated (more than kPlainSumsMaxBins bins) or plain.
+template <bool DERIV, bool D2 = false, bool COMP = true>
 __global__ void __launch_bounds__(kMlpBlock) kv_plain_f32_kernel(MlpPathParams p, int max_iter)
 {
     const int t = threadIdx.x;
@@ -638,7 +639,7 @@ __global__ void __launch_bounds__(kMlpBlock) kv_plain_f32_kernel(MlpPathParams p
         PeakConst c = peak_constants(va, xa, tp, g_exp_tab);
         float t0, t1;
         const bool ok = range_alg12_f32(c.b, tp, p.log_eps, max_iter, t0, t1, capped);
-        pair_tail<DERIV, D2>(p, i, active, edge, ok, v, x, c, t0, t1, capped ? KV_PAIR_RANGE_CAP : KV_PAIR_OK);
+        pair_tail<DERIV, D2, COMP>(p, i, active, edge, ok, v, x, c, t0, t1, capped ? KV_PAIR_RANGE_CAP : KV_PAIR_OK);
     }
 }
 
@@ -650,8 +651,9 @@ __global__ void __launch_bounds__(kMlpBlock) kv_plain_f32_kernel(MlpPathParams p
 // reads TMEM lanes 32w..32w+31 (its own pairs' rows) and finishes layer 3 in registers.  (Layer
 // 3 on the tensor cores as well measured slower: the second MMA round trip per tile costs more
 // than the 128 FMAs it saves.)  A wait that does not finish within its limit sends the CTA's
-// remaining pairs to the fallback list (correct, slower) instead of hanging.
-template <bool DERIV, bool D2 = false>
+// remaining pairs to the fallback list (correct, slower) instead of hanging.  COMP: the bins'
+// block sums compensated (more than kPlainSumsMaxBins bins) or plain.
+template <bool DERIV, bool D2 = false, bool COMP = true>
 __global__ void __launch_bounds__(kMlpBlock, D2 ? 6 : 8) kv_mlp_tc_kernel(MlpPathParams p)
 {
     __shared__ __align__(1024) TcSmem sm;
@@ -764,7 +766,7 @@ __global__ void __launch_bounds__(kMlpBlock, D2 ? 6 : 8) kv_mlp_tc_kernel(MlpPat
         const float w1 = fmaxf(fmaxf(__expf(L1) - DELTA, 0.0f) + (tp - tr), 1e-6f * (1.0f + tr));
         float t0, t1;
         const bool ok = check_range(c.b, tr, w0, w1, p.log_eps, lo_ok, t0, t1);
-        pair_tail<DERIV, D2>(p, i, active, edge, ok, v, x, c, t0, t1);
+        pair_tail<DERIV, D2, COMP>(p, i, active, edge, ok, v, x, c, t0, t1);
     }
     if (aborted) {
         // a tensor-core wait ran out: the remaining pairs of this CTA go to the fallback pass
@@ -1264,12 +1266,15 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
     cudaError_t e = cudaMemsetAsync(p.fb_count, 0, sizeof(uint32_t), s);
     const bool second = a->d2v || a->dvx || a->d2x;
     const bool deriv = a->dv || a->dx || second;
+    const bool plain = bins <= kPlainSumsMaxBins;  // few enough bins per lane for plain block sums
     if (e == cudaSuccess && f32_plain) {
         int64_t need = (a->n + kMlpBlock - 1) / kMlpBlock;
         int64_t cap = (int64_t)sm_count() * 16;
         int grid = (int)(need < cap ? need : cap);
         if (second) kv_plain_f32_kernel<true, true><<<grid, kMlpBlock, 0, s>>>(p, max_iter);
+        else if (deriv && plain) kv_plain_f32_kernel<true, false, false><<<grid, kMlpBlock, 0, s>>>(p, max_iter);
         else if (deriv) kv_plain_f32_kernel<true><<<grid, kMlpBlock, 0, s>>>(p, max_iter);
+        else if (plain) kv_plain_f32_kernel<false, false, false><<<grid, kMlpBlock, 0, s>>>(p, max_iter);
         else kv_plain_f32_kernel<false><<<grid, kMlpBlock, 0, s>>>(p, max_iter);
         note_launch();
         e = cudaGetLastError();
@@ -1282,7 +1287,9 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
         int64_t cap = (int64_t)sm_count() * per_sm;
         int grid = (int)(need < cap ? need : cap);
         if (second) kv_mlp_tc_kernel<true, true><<<grid, kMlpBlock, 0, s>>>(p);
+        else if (deriv && plain) kv_mlp_tc_kernel<true, false, false><<<grid, kMlpBlock, 0, s>>>(p);
         else if (deriv) kv_mlp_tc_kernel<true><<<grid, kMlpBlock, 0, s>>>(p);
+        else if (plain) kv_mlp_tc_kernel<false, false, false><<<grid, kMlpBlock, 0, s>>>(p);
         else kv_mlp_tc_kernel<false><<<grid, kMlpBlock, 0, s>>>(p);
         note_launch();
         e = cudaGetLastError();

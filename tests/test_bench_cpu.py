@@ -13,6 +13,9 @@ def test_bench_module_imports_and_defines_counts():
     import bench
 
     assert bench.FP32_OPS_PER_BIN > 0 and bench.FP32_OPS_PER_PAIR > 0
+    # the instance with plain block sums below the threshold, compensated sums above it
+    assert bench.fp32_ops(bench.PLAIN_SUMS_MAX_BINS) == bench.FP32_OPS_PER_PAIR + (bench.PLAIN_SUMS_MAX_BINS + 1) * bench.FP32_OPS_PER_BIN
+    assert bench.fp32_ops(64) == bench.FP32_OPS_PER_PAIR_COMP + 65 * bench.FP32_OPS_PER_BIN_COMP
     assert callable(bench._env_rank) and callable(bench.all_reduce_scalar)
     # the SFU figure of the 16.7M-pair step at 32 bins, 1.273 ms, 152 SMs at 2070 MHz
     s = bench.sfu_utilisation(16_777_216, 32, 1.273, 152, 2070.0)
@@ -93,3 +96,16 @@ def test_counts_source_hash_is_current_or_flagged():
     h = bench.counts_source_sha()
     assert isinstance(h, str) and len(h) == 16
     assert isinstance(bench.COUNTS_SOURCE_SHA, str) and len(bench.COUNTS_SOURCE_SHA) == 16
+
+
+def test_plain_sums_threshold_matches_the_kernels():
+    """The bench picks the operation counts of the kernel instance that runs: its threshold must
+    be the kernels' own (kPlainSumsMaxBins in kv_bins.cuh)."""
+    import re
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    with open(os.path.join(ROOT, "paper_2108_11560_gb300", "csrc", "kv_bins.cuh")) as f:
+        m = re.search(r"constexpr int kPlainSumsMaxBins = (\d+);", f.read())
+    assert m and int(m.group(1)) == bench.PLAIN_SUMS_MAX_BINS

@@ -157,7 +157,7 @@ def test_trained_network_fits_its_targets(net):
     assert np.median(e1) < 0.03 and np.quantile(e1, 0.99) < 0.2
 
 
-@pytest.mark.parametrize("bins", [32, 40])
+@pytest.mark.parametrize("bins", [32, 40, 41])
 def test_mlp_path_matches_oracle(net, bins):
     """The fast path on the hard-band and learned-bracket workloads against the oracle's method
     (FP64 ... long double) and the dense truth; every pair, fallback or not."""
