@@ -67,41 +67,41 @@ F64_SLICE = 1 << 23     # the FP64 path's slice of the workload (134 MB of float
 
 # Algorithmic FP32 work of the learned-bracket fast path, counted operation by operation from
 # its formulas with an FMA as one operation and a paired (f32x2) instruction as two:
-#   per bin: the abscissa 1, the exponent's x-part (the phi polynomials or e^{+-s}) 15, the rest
-#            of the weight 5, the two derivative integrands 7 (+ the tanh polynomial in the ~33 %
-#            of warp-blocks that need it, ~2.7), three block-compensated sums 5.25
-#                                                                               -> 36 (+ 4 MUFU)
+#   per bin: the abscissa 1, the exponent's x-part (the phi polynomials, or x cosh t from e^{+-s},
+#            which the d/dx integrand shares) 16, the rest of the weight 5, the two derivative
+#            integrands 5 (+ the tanh polynomial in the ~33 % of warp-blocks that need it, ~2.7),
+#            three sums 3 (plain block sums) or 5.25 (compensated)     -> 32.7 or 35 (+ 4 MUFU)
 #   per pair: layer 1 and layer 3 on the CUDA cores 256 (layer 2 runs on the tensor cores and
-#             is not counted), peak Newton, offset constants, endpoint check, setup and finish
-#             ~250                                                              -> 505
+#             is not counted), one peak Newton step, offset constants, endpoint check, setup and
+#             finish ~225                                                       -> 482
 # ncu's executed FFMA + FADD + FMUL (+ 2 x FFMA2/FADD2/FMUL2) counters over 4M hard-band pairs (one
 # launch of the fast-path kernel each) give these per bin and per pair: for the kernel instance
 # with plain block sums (up to PLAIN_SUMS_MAX_BINS bins), from launches at 1 and 32 bins; for the
 # instance with compensated block sums (more bins), from launches at 41 and 64 bins.
 PLAIN_SUMS_MAX_BINS = 40
-FP32_OPS_PER_BIN = 33.886
-FP32_OPS_PER_PAIR = 488.22
-FP32_OPS_PER_BIN_COMP = 35.703
-FP32_OPS_PER_PAIR_COMP = 518.20
+FP32_OPS_PER_BIN = 32.886
+FP32_OPS_PER_PAIR = 482.27
+FP32_OPS_PER_BIN_COMP = 34.703
+FP32_OPS_PER_PAIR_COMP = 512.27
 MUFU_OPS_PER_BIN = 4
 # XU-pipe (MUFU) operations per pair outside the bins from the same captures
-# (smsp__inst_executed_pipe_xu x 32: 47.2 per pair at 1 bin, 4.0 per bin), and the XU pipe's lanes
-# per SM per clock that ncu's XU percentages are taken against (171.2 operations per pair in
-# 0.320 ms per 4M pairs read as 24 percent there).
-MUFU_OPS_PER_PAIR = 39.2
+# (smsp__inst_executed_pipe_xu x 32: 43.2 per pair at 1 bin, 4.0 per bin), and the XU pipe's lanes
+# per SM per clock that ncu's XU percentages are taken against (167.2 operations per pair in
+# 0.280 ms per 4M pairs read as 27 percent of the active cycles there).
+MUFU_OPS_PER_PAIR = 35.18
 XU_LANES_PER_SM = 32
 # DRAM bytes per pair of the fast-path kernel (read + write) from an ncu capture of one full
 # 16,777,216-pair launch at 32 bins in steady state (the fourth of five consecutive launches, no
 # cache flush between them, so the previous launch's outputs are written back inside it):
-# 201.38 MB read + 199.85 MB written.  The algorithmic bytes per pair are v, x, grad_out in and
+# 201.43 MB read + 198.81 MB written.  The algorithmic bytes per pair are v, x, grad_out in and
 # log K, d/dv, d/dx out, 4 bytes each (402.65 MB per launch).
-TRAFFIC_BYTES_PER_PAIR = (201.38e6 + 199.85e6) / 16777216
+TRAFFIC_BYTES_PER_PAIR = (201.43e6 + 198.81e6) / 16777216
 ALGORITHMIC_BYTES_PER_PAIR = 24
 # The counts above hold for the fast-path kernel built from these sources; COUNTS_SOURCE_SHA is
 # their hash when the counts were taken.  When the sources change, the line says so and reports
 # no traffic until the counters are taken again.
 COUNTS_SOURCES = ("kv_mlp.cu", "kv_bins.cuh", "kv_dfloat.cuh")
-COUNTS_SOURCE_SHA = "a6ba49e6ccc71c00"
+COUNTS_SOURCE_SHA = "a36ed0da5394154a"
 
 PATHS = {
     # name: (bracket, second derivatives, float64 I/O)

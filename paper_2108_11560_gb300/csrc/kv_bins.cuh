@@ -286,6 +286,30 @@ __device__ __forceinline__ float delta_g_slope_f32(const BinsF& b, float e2, flo
     return b.c1 + dl - b.ap * (es - 1.0f) + b.am * (ems - 1.0f);
 }
 
+// delta_g_coarse and delta_g_slope_f32 at two points at once (paired instructions; the
+// exponentials per component).
+__device__ __forceinline__ float2 delta_g_coarse2(const BinsF& b, float2 s, float2& e2, float2& es,
+                                                  float2& ems)
+{
+    const float2 el = mul2(s, f2(LOG2E_F));
+    es = make_float2(ex2_approx(el.x), ex2_approx(el.y));
+    ems = make_float2(rcp_approx(es.x), rcp_approx(es.y));
+    const float2 ea = mul2(fma2(f2(b.v), s, f2(b.u)), f2(-2.0f * LOG2E_F));
+    e2 = make_float2(ex2_approx(ea.x), ex2_approx(ea.y));
+    const float2 ope = add2(f2(1.0f), e2);
+    const float2 d = fma2(make_float2(lg2_approx(ope.x), lg2_approx(ope.y)), f2(LN2_F), f2(-b.lu));
+    const float2 php = fma2(s, f2(-1.0f), add2(es, f2(-1.0f)));  // (e^s - 1) - s
+    const float2 phm = add2(add2(ems, f2(-1.0f)), s);            // (e^-s - 1) + s
+    return fma2(f2(-b.ap), php, fma2(f2(-b.am), phm, fma2(f2(b.c1), s, d)));
+}
+
+__device__ __forceinline__ float2 delta_g_slope2(const BinsF& b, float2 e2, float2 es, float2 ems)
+{
+    const float2 ope = add2(f2(1.0f), e2);
+    const float2 dl = mul2(mul2(f2(-2.0f * b.v), e2), make_float2(rcp_approx(ope.x), rcp_approx(ope.y)));
+    return fma2(f2(-b.ap), add2(es, f2(-1.0f)), fma2(f2(b.am), add2(ems, f2(-1.0f)), add2(f2(b.c1), dl)));
+}
+
 // The bin constants rescaled once per pair so that a bin works in base-2 exponent units.  The
 // weight is split as
 //   e^{g(t) - g(t_p)} = e^{-lu} (1 + e^{-2vt}) 2^{c1 s + N(s)},   lu = log1p(e^{-2u}),
@@ -300,6 +324,7 @@ struct BinsK {
     float nap, nam;        // -ap, -am
     float nv2, nu2;        // -2 v log2 e, -2 u log2 e: e^{-2vt} = 2^{nv2 s + nu2}
     float kc;              // e^{-lu} = 1 / (1 + e^{-2u})
+    float s2;              // -1 / (x log2 e) = -cosh t_p / cA: turns sum w nxc into sum w cosh t
 };
 
 __device__ __forceinline__ BinsK bins_k(const BinsF& b)
@@ -320,14 +345,18 @@ __device__ __forceinline__ BinsK bins_k(const BinsF& b)
     k.nv2 = -2.0f * LOG2E_F * b.v;
     k.nu2 = -2.0f * LOG2E_F * b.u;
     k.kc = ex2_approx(-k.lu);  // e^{-lu} from the same lu as the offset g(t_p), which it cancels
+    k.s2 = -(k.hep + k.hem) * rcp_approx(k.cA);
     return k;
 }
 
 // N(s) for two bins:
 //   |s| <= 1: phi(+-s) = z (E(z) +- s O(z)), so N = -z (x cosh t_p E + x sinh t_p s O);
-//   |s| > 1:  N = -(x e^{t_p}/2) e^s - (x e^{-t_p}/2) e^{-s} + x sinh t_p s + x cosh t_p;
-// (all times log2 e); e^{+-s} (es, ems) are returned for the cosh t integrand.
-__device__ __forceinline__ float2 x_part2(const BinsK& k, float2 s, float2& es, float2& ems)
+//   |s| > 1:  N = x cosh t_p + x sinh t_p s - x cosh t  with  x cosh t = (x e^{t_p}/2) e^s + (x e^{-t_p}/2) e^{-s}
+// (all times log2 e).  With DERIV, nxc = -(x cosh t) log2 e is returned for the d/dx integrand
+// (w cosh t = w nxc times -1/(x log2 e), applied once to the sum), so that the cosh t of the
+// integrand and the exponent share their products.
+template <bool DERIV>
+__device__ __forceinline__ float2 x_part2(const BinsK& k, float2 s, float2& nxc)
 {
     const float2 z = mul2(s, s);
     float2 E, O;
@@ -335,21 +364,34 @@ __device__ __forceinline__ float2 x_part2(const BinsK& k, float2 s, float2& es, 
     const float2 so = mul2(s, O);
     const float2 ns = mul2(z, fma2(f2(k.nA), E, mul2(f2(k.nB), so)));
     const float2 el = mul2(s, f2(LOG2E_F));
-    es = make_float2(ex2_approx(el.x), ex2_approx(el.y));
-    ems = make_float2(rcp_approx(es.x), rcp_approx(es.y));
-    const float2 nl = fma2(f2(k.nap), es, fma2(f2(k.nam), ems, fma2(f2(k.cB), s, f2(k.cA))));
+    const float2 es = make_float2(ex2_approx(el.x), ex2_approx(el.y));
+    const float2 ems = make_float2(rcp_approx(es.x), rcp_approx(es.y));
+    float2 nl;
+    if constexpr (DERIV) {
+        nxc = fma2(f2(k.nap), es, mul2(f2(k.nam), ems));
+        nl = add2(fma2(f2(k.cB), s, f2(k.cA)), nxc);
+    } else {
+        nl = fma2(f2(k.nap), es, fma2(f2(k.nam), ems, fma2(f2(k.cB), s, f2(k.cA))));
+    }
     return make_float2(fabsf(s.x) <= PHI_SERIES_MAX ? ns.x : nl.x, fabsf(s.y) <= PHI_SERIES_MAX ? ns.y : nl.y);
 }
 
-__device__ __forceinline__ float x_part(const BinsK& k, float s, float& es, float& ems)
+template <bool DERIV>
+__device__ __forceinline__ float x_part(const BinsK& k, float s, float& nxc)
 {
     const float z = s * s;
     float E, O;
     KV_PHI_SERIES(__fmul_rn, fmaf, f1, z, E, O)
     const float ns = z * fmaf(k.nA, E, k.nB * (s * O));
-    es = ex2_approx(s * LOG2E_F);
-    ems = rcp_approx(es);
-    const float nl = fmaf(k.nap, es, fmaf(k.nam, ems, fmaf(k.cB, s, k.cA)));
+    const float es = ex2_approx(s * LOG2E_F);
+    const float ems = rcp_approx(es);
+    float nl;
+    if constexpr (DERIV) {
+        nxc = fmaf(k.nap, es, k.nam * ems);
+        nl = fmaf(k.cB, s, k.cA) + nxc;
+    } else {
+        nl = fmaf(k.nap, es, fmaf(k.nam, ems, fmaf(k.cB, s, k.cA)));
+    }
     return fabsf(s) <= PHI_SERIES_MAX ? ns : nl;
 }
 
@@ -366,8 +408,8 @@ __device__ __forceinline__ void bin_f32(const BinsF& b, const BinsK& k, float mf
                                         float& w1, float& w2)
 {
     const float s = fmaf(mf, b.h, b.s0);
-    float es, ems;
-    const float N = x_part(k, s, es, ems);
+    float nxc;
+    const float N = x_part<DERIV>(k, s, nxc);
     const float ea = fmaf(k.nv2, s, k.nu2);
     const float e2 = ex2_approx(ea);  // e^{-2vt}
     const float ope = 1.0f + e2;
@@ -380,7 +422,7 @@ __device__ __forceinline__ void bin_f32(const BinsF& b, const BinsK& k, float mf
         if (!VOTE || __any_sync(0xffffffffu, small))
             q = small ? tanh_small(ea * (-0.5f * LN2_F)) * ope : q;
         w1 = wp * (t * q);
-        w2 = w * fmaf(k.hep, es, k.hem * ems);  // w cosh t
+        w2 = w * nxc;  // w cosh t times -x log2 e
     }
 }
 
@@ -400,8 +442,8 @@ __device__ __forceinline__ void bin_f32x2(const BinsF& b, const BinsK& k, float2
                                           float2& w1, float2& w2)
 {
     const float2 s = fma2(mf, f2(b.h), f2(b.s0));
-    float2 es, ems;
-    const float2 N = x_part2(k, s, es, ems);
+    float2 nxc;
+    const float2 N = x_part2<DERIV>(k, s, nxc);
     const float2 ea = fma2(f2(k.nv2), s, f2(k.nu2));
     const float2 e2 = make_float2(ex2_approx(ea.x), ex2_approx(ea.y));  // e^{-2vt}
     const float2 ope = add2(f2(1.0f), e2);
@@ -417,7 +459,7 @@ __device__ __forceinline__ void bin_f32x2(const BinsF& b, const BinsK& k, float2
             q = make_float2(kx ? tq.x : q.x, ky ? tq.y : q.y);
         }
         w1 = mul2(wp, mul2(t, q));
-        w2 = mul2(w, fma2(f2(k.hep), es, mul2(f2(k.hem), ems)));  // w cosh t
+        w2 = mul2(w, nxc);  // w cosh t times -x log2 e
     }
 }
 
@@ -483,7 +525,7 @@ __device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, fl
     }
     S0 = lane_sum<float, L>(k0.value());
     S1 = DERIV ? lane_sum<float, L>(k1.value()) : 0.0f;
-    S2 = DERIV ? lane_sum<float, L>(k2.value()) : 0.0f;
+    S2 = DERIV ? lane_sum<float, L>(k2.value()) * k.s2 : 0.0f;
 }
 
 // ------------------------------------------------------------------ second derivatives

@@ -68,6 +68,46 @@ __device__ __forceinline__ void eval_F_f32(float v, float x, const BinsF& b, flo
     else eval_h_f32(b, le, t, F, dF);
 }
 
+// The same functions at two points at once (the bisection and Newton points of one FindZero
+// iteration), in paired FP32 instructions.
+__device__ __forceinline__ void eval_g1_g2_f32x2(float v, float x, float2 t, float2& F, float2& dF)
+{
+    const float2 vt = mul2(f2(v), t);
+    const float2 ea = mul2(vt, f2(-2.0f * LOG2E_F));
+    const float2 e2 = make_float2(ex2_approx(ea.x), ex2_approx(ea.y));
+    const float2 ope = add2(f2(1.0f), e2);
+    const float2 r = make_float2(rcp_approx(ope.x), rcp_approx(ope.y));
+    const float2 thl = mul2(fma2(e2, f2(-1.0f), f2(1.0f)), r);
+    const float2 thz = mul2(vt, vt);
+    float2 thp;
+    KV_TANH_POLY(fma2, f2, thz, thp)
+    const float2 ths = fma2(mul2(vt, thz), thp, vt);
+    const float2 th = make_float2(vt.x < TANH_SERIES_MAX ? ths.x : thl.x, vt.y < TANH_SERIES_MAX ? ths.y : thl.y);
+    const float2 el = mul2(t, f2(LOG2E_F));
+    const float2 et = make_float2(ex2_approx(el.x), ex2_approx(el.y));
+    const float2 eti = make_float2(rcp_approx(et.x), rcp_approx(et.y));
+    const float2 z = mul2(t, t);
+    const float2 ss = mul2(t, fma2(z, fma2(z, fma2(z, f2(1.0f / 5040.0f), f2(1.0f / 120.0f)), f2(1.0f / 6.0f)), f2(1.0f)));
+    const float2 shl = mul2(fma2(eti, f2(-1.0f), et), f2(0.5f));
+    const float2 sh = make_float2(t.x < 0.5f ? ss.x : shl.x, t.y < 0.5f ? ss.y : shl.y);
+    const float2 ch = mul2(add2(et, eti), f2(0.5f));
+    F = fma2(f2(v), th, mul2(f2(-x), sh));
+    dF = fma2(f2(v * v), mul2(mul2(f2(4.0f), e2), mul2(r, r)), mul2(f2(-x), ch));
+}
+
+template <int KIND>
+__device__ __forceinline__ void eval_F_f32x2(float v, float x, const BinsF& b, float le, float2 t, float2& F,
+                                             float2& dF)
+{
+    if (KIND == 0) {
+        eval_g1_g2_f32x2(v, x, t, F, dF);
+    } else {
+        float2 e2, es, ems;
+        F = add2(delta_g_coarse2(b, add2(t, f2(-b.tp)), e2, es, ems), f2(-le));
+        dF = delta_g_slope2(b, e2, es, ems);
+    }
+}
+
 // Algorithm 1 in FP32; returns false when the doubling cap was hit before the sign changed.
 template <int KIND>
 __device__ __forceinline__ bool find_range_f32(float v, float x, const BinsF& b, float le, float t0,
@@ -94,10 +134,10 @@ __device__ __forceinline__ bool find_range_f32(float v, float x, const BinsF& b,
 }
 
 // Algorithm 2 in FP32 with a fixed trip count.  Each iteration evaluates F at both the bisection
-// point and the Newton point and selects the update with predicates (the Newton point's value is
-// used only where the bisection point is on the positive side, as in the algorithm): lanes of a
-// warp that would take different sides of the test then run the same instructions instead of
-// running the two sides one after the other.
+// point and the Newton point, together in paired instructions, and selects the update with
+// predicates (the Newton point's value is used only where the bisection point is on the positive
+// side, as in the algorithm): lanes of a warp that would take different sides of the test then
+// run the same instructions instead of running the two sides one after the other.
 template <int KIND>
 __device__ __forceinline__ float find_zero_f32(float v, float x, const BinsF& b, float le, float t_neg,
                                                float t_pos, float Fa, float dFa, int max_iter)
@@ -108,9 +148,9 @@ __device__ __forceinline__ float find_zero_f32(float v, float x, const BinsF& b,
         float newton = a - __fdividef(Fa, dFa);
         newton = isfinite(newton) ? newton : shrink;
         newton = fminf(fmaxf(newton, fminf(t_neg, shrink)), fmaxf(t_neg, shrink));
-        float Fs, dFs, Fn, dFn;
-        eval_F_f32<KIND>(v, x, b, le, shrink, Fs, dFs);
-        eval_F_f32<KIND>(v, x, b, le, newton, Fn, dFn);
+        float2 F2, dF2;
+        eval_F_f32x2<KIND>(v, x, b, le, make_float2(shrink, newton), F2, dF2);
+        const float Fs = F2.x, dFs = dF2.x, Fn = F2.y, dFn = dF2.y;
         const bool s_neg = Fs < 0.0f;           // the bisection point becomes the negative end
         const bool n_neg = !s_neg && Fn < 0.0f;  // else the Newton point does, if negative
         a = s_neg ? shrink : (n_neg ? newton : a);

@@ -525,25 +525,17 @@ __global__ void __launch_bounds__(kSumBlock) kv_sum_final(const double* part, in
 // ------------------------------------------------------------------ host side
 
 template <typename K>
-int resident_blocks(K kernel, int block)
-{
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, block, 0) != cudaSuccess || b < 1)
-        b = 1;
-    cudaGetLastError();
-    return b;
-}
-
-template <typename K>
 int launch_pairs(K kernel, const KParams& p, int pairs_per_warp, cudaStream_t s)
 {
-    // persistent grid of at most the resident blocks of every SM; a block's four warps run on
-    // the SM's four sub-partitions
+    // one block per kBlock / 32 warps' pairs (a block's four warps run on the SM's four
+    // sub-partitions): the block scheduler hands each SM a new block as one finishes, where a
+    // persistent grid with a fixed share per block ends with SMs running fewer and fewer blocks
+    // (the blocks resident on one SM get unequal shares of its issue slots).  Beyond the largest
+    // grid the kernels' grid-stride loops take the rest.
     const int64_t warps = (p.n + pairs_per_warp - 1) / pairs_per_warp;
     const int block = kBlock;
     const int64_t need = (warps * 32 + block - 1) / block;
-    const int64_t cap = (int64_t)kvh::sm_count() * resident_blocks(kernel, block);
-    int grid = (int)(need < cap ? need : cap);
+    int grid = (int)(need < 0x7fffffffll ? need : 0x7fffffffll);
     if (grid < 1) grid = 1;
     kernel<<<grid, block, 0, s>>>(p);
     KV_LAUNCH_CHECK();

@@ -155,14 +155,15 @@ __device__ __forceinline__ float fast_asinh(float z)
     return __logf(fmaf(q, r, z));
 }
 
-// The peak of g by STEPS FP32 Newton steps from asinh(v/x) (0 when v^2 <= x).  On the fast path
-// (two steps: a third changed neither the fallback rate nor the results) its accuracy does not
-// enter the results (the bins are exact relative to any
-// reference point near the peak); the training targets and the raw predictions, which are
+// The peak of g by STEPS FP32 Newton steps from the least of three upper bounds (0 when
+// v^2 <= x).  On the fast path (one step: a second changed neither the fallback rate, 0 on the
+// hard band and 3.7e-4 on the extreme range, nor the accuracy) its accuracy does not enter the
+// results: the bins are exact relative to any reference point near the peak, and the range check
+// tests the predicted ends themselves.  The training targets and the raw predictions, which are
 // measured from the peak, take eight.  The steps use the approximate exponential, reciprocal and
 // division.  The start is nudged up so that it stays on the side of the zero where g' <= 0
 // despite the approximate asinh.
-template <int STEPS = 2>
+template <int STEPS>
 __device__ __forceinline__ float peak_f32(float v, float x)
 {
     if (!(v * v > x)) return 0.0f;
@@ -377,6 +378,7 @@ struct MlpPathParams {
     float log_eps;
     uint32_t* fb_list;
     uint32_t* fb_count;
+    uint32_t* tile_ctr;  // tiles claimed beyond each CTA's first (zero at launch)
     kvh::MlpView mlp;
     MlpConst wc;
     int wait_limit;  // iterations of the per-tile wait for the tensor-core results
@@ -438,11 +440,17 @@ __device__ __forceinline__ bool check_range(const BinsF& b, float tr, float w0, 
     if (tr > 0.0f) {
         // the left end: the predicted one, or 0 when the range reaches it
         float s0 = -fminf(w0, tr);
-        const float dz = delta_g_coarse(b, -tr, e2, es, ems);  // at t = 0
+        // at t = 0 and at the predicted left end, together
+        float2 e2p, esp, emsp;
+        const float2 dzp = delta_g_coarse2(b, make_float2(-tr, s0), e2p, esp, emsp);
+        const float dz = dzp.x;
         if (dz > le || (s0 <= -tr && dz >= lo)) {
             t0 = 0.0f;  // the range starts at 0 and is not too wide there
         } else {
-            float d0 = s0 <= -tr ? dz : delta_g_coarse(b, s0, e2, es, ems);
+            float d0 = s0 <= -tr ? dz : dzp.y;
+            e2 = e2p.y;
+            es = esp.y;
+            ems = emsp.y;
             for (int k = 0; k < kNewtonSteps && !in_window(d0) && s0 > -tr; ++k) {
                 const float slope = delta_g_slope_f32(b, e2, es, ems);
                 float sn = s0 - (d0 - mid) / slope;
@@ -492,6 +500,7 @@ struct TcSmem {
     unsigned char bb[H * 16 * 2];    // B of layer 2's extra K slice: k = 0, 1 hold b2 split hi + lo
     unsigned char ones[8 * 16 * 2];  // A of that slice, one 8-row group read by every group: 1, 1, 0...
     uint64_t mbar;
+    uint32_t next_tile;  // the tile thread 0 claimed for the CTA's next trip
     uint32_t tmem;
 };
 
@@ -643,16 +652,18 @@ __global__ void __launch_bounds__(kMlpBlock) kv_plain_f32_kernel(MlpPathParams p
     }
 }
 
-// The fast path with the hidden layer on the tensor cores.  Each CTA of 128 threads takes 128
-// pairs per trip (one per thread): layer 1 on the CUDA cores writes h1 as BF16 into a K-major
-// shared tile; one elected thread issues five tcgen05.mma (M = 128, N = 64, K = 16; the fifth
-// multiplies a column of ones by b2 split into two BF16 parts, so the bias comes out of the
-// tensor cores too) into 64 TMEM columns and commits them to an mbarrier; after the wait, warp w
-// reads TMEM lanes 32w..32w+31 (its own pairs' rows) and finishes layer 3 in registers.  (Layer
-// 3 on the tensor cores as well measured slower: the second MMA round trip per tile costs more
-// than the 128 FMAs it saves.)  A wait that does not finish within its limit sends the CTA's
-// remaining pairs to the fallback list (correct, slower) instead of hanging.  COMP: the bins'
-// block sums compensated (more than kPlainSumsMaxBins bins) or plain.
+// The fast path with the hidden layer on the tensor cores.  Each CTA of 128 threads takes a tile
+// of 128 pairs per trip (one per thread; the tiles after the first claimed from a global
+// counter): layer 1 on the CUDA cores writes h1 as BF16 into a K-major shared tile; one
+// elected thread issues five tcgen05.mma (M = 128, N = 64, K = 16; the fifth multiplies a column
+// of ones by b2 split into two BF16 parts, so the bias comes out of the tensor cores too) into 64
+// TMEM columns and commits them to an mbarrier; after the wait, warp w reads TMEM lanes
+// 32w..32w+31 (its own pairs' rows) and finishes layer 3 in registers.  (Layer 3 on the tensor
+// cores as well measured slower, also with its MMAs overlapped with the previous tile's bins: the
+// second round trip and barrier per tile cost about what the 128 FMAs save.)  A wait that does not
+// finish within its limit sends the CTA's remaining pairs and every tile still unclaimed to the
+// fallback list (correct, slower) instead of hanging.  COMP: the bins' block sums compensated
+// (more than kPlainSumsMaxBins bins) or plain.
 template <bool DERIV, bool D2 = false, bool COMP = true>
 __global__ void __launch_bounds__(kMlpBlock, D2 ? 6 : 8) kv_mlp_tc_kernel(MlpPathParams p)
 {
@@ -689,21 +700,25 @@ __global__ void __launch_bounds__(kMlpBlock, D2 ? 6 : 8) kv_mlp_tc_kernel(MlpPat
     const float lo_ok = p.log_eps - (float)kWindow;
     uint32_t phase = 0;
     bool aborted = false;
-    int64_t base = (int64_t)blockIdx.x * kMlpBlock;
-    const int64_t stride = (int64_t)gridDim.x * kMlpBlock;
+    // Tiles are handed out dynamically: each CTA starts with tile blockIdx.x and claims every
+    // further tile from a global counter, one trip ahead (thread 0, published to the CTA at the
+    // tile's first barrier).  The CTAs resident on one SM get unequal shares of its issue slots,
+    // so a fixed share of tiles per CTA leaves the SM with fewer and fewer CTAs towards the end.
+    // (tile indices fit 32 bits: the path takes at most 2^32 pairs)
+    const uint32_t ntiles = (uint32_t)((p.n + kMlpBlock - 1) / kMlpBlock);
+    uint32_t tile = blockIdx.x;
+    uint32_t next = ntiles;
     // this thread's inputs of the next tile are loaded one tile ahead, so their DRAM latency
     // overlaps the current tile's work
-    float v_next = base + t < p.n ? __ldcs(p.v + base + t) : 1.0f;
-    float x_next = base + t < p.n ? __ldcs(p.x + base + t) : 1.0f;
-    for (; base < p.n; base += stride) {
-        const int64_t i = base + t;
+    float v_next = (int64_t)tile * kMlpBlock + t < p.n ? __ldcs(p.v + (int64_t)tile * kMlpBlock + t) : 1.0f;
+    float x_next = (int64_t)tile * kMlpBlock + t < p.n ? __ldcs(p.x + (int64_t)tile * kMlpBlock + t) : 1.0f;
+    for (; tile < ntiles; tile = next) {
+        const int64_t i = (int64_t)tile * kMlpBlock + t;
         const bool active = i < p.n;
         const float v = v_next;
         const float x = x_next;
-        if (i + stride < p.n) {
-            v_next = __ldcs(p.v + i + stride);
-            x_next = __ldcs(p.x + i + stride);
-        }
+        uint32_t claimed = 0;
+        if (t == 0) claimed = atomicAdd(p.tile_ctr, 1u);
         float lk, dv, dx;
         const bool edge = float_edge(v, x, lk, dv, dx);
         const float va = edge ? 1.0f : fabsf(v);
@@ -725,7 +740,13 @@ __global__ void __launch_bounds__(kMlpBlock, D2 ? 6 : 8) kv_mlp_tc_kernel(MlpPat
                 *reinterpret_cast<uint4*>(sm.a + tile_off(t, 8 * c)) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
             }
         }
+        if (t == 0) sm.next_tile = min(gridDim.x + claimed, ntiles);
         sync_for_mma();
+        next = sm.next_tile;
+        if ((int64_t)next * kMlpBlock + t < p.n) {
+            v_next = __ldcs(p.v + (int64_t)next * kMlpBlock + t);
+            x_next = __ldcs(p.x + (int64_t)next * kMlpBlock + t);
+        }
         if (t == 0) {  // layer 2: h1 W2^T + 1 (b2 hi + b2 lo)
 #pragma unroll
             for (int kk = 0; kk < H / 16; ++kk)
@@ -758,7 +779,7 @@ __global__ void __launch_bounds__(kMlpBlock, D2 ? 6 : 8) kv_mlp_tc_kernel(MlpPat
         // separately, once per group.
         const float L0 = fmaf(y0, p.wc.out_scale[0], p.wc.out_scale[1]);
         const float L1 = fmaf(y1, p.wc.out_scale[2], p.wc.out_scale[3]);
-        const float tp = peak_f32(va, xa);
+        const float tp = peak_f32<1>(va, xa);
         PeakConst c = peak_constants(va, xa, tp, g_exp_tab);
         const float tr = c.b.tp;  // the grid point next to tp: the bins' reference
         // the predicted range [tp - w0, tp + w1] as distances below and above tr
@@ -769,13 +790,20 @@ __global__ void __launch_bounds__(kMlpBlock, D2 ? 6 : 8) kv_mlp_tc_kernel(MlpPat
         pair_tail<DERIV, D2, COMP>(p, i, active, edge, ok, v, x, c, t0, t1);
     }
     if (aborted) {
-        // a tensor-core wait ran out: the remaining pairs of this CTA go to the fallback pass
-        for (int64_t b2 = base; b2 < p.n; b2 += (int64_t)gridDim.x * kMlpBlock) {
-            const int64_t i = b2 + t;
+        // a tensor-core wait ran out: this tile, the one claimed for the next trip and every tile
+        // still unclaimed go to the fallback pass
+        for (;;) {
+            const int64_t i = (int64_t)tile * kMlpBlock + t;
             if (i < p.n) {
                 uint32_t k = atomicAdd(p.fb_count, 1u);
                 p.fb_list[k] = (uint32_t)i;
             }
+            tile = next;
+            if (tile >= ntiles) break;
+            __syncthreads();
+            if (t == 0) sm.next_tile = min(gridDim.x + atomicAdd(p.tile_ctr, 1u), ntiles);
+            __syncthreads();
+            next = sm.next_tile;
         }
         mbar_wait(&sm.mbar, phase);  // let the MMA in flight finish before its TMEM goes (full bound)
     }
@@ -1262,15 +1290,15 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
     uint32_t* scratch = scratch_in;
     if (!scratch) KV_CUDA_TRY(scratch_alloc((void**)&scratch, sizeof(uint32_t) * (a->n + 32), s));
     p.fb_count = scratch;
+    p.tile_ctr = scratch + 1;
     p.fb_list = scratch + 32;
-    cudaError_t e = cudaMemsetAsync(p.fb_count, 0, sizeof(uint32_t), s);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 2 * sizeof(uint32_t), s);
     const bool second = a->d2v || a->dvx || a->d2x;
     const bool deriv = a->dv || a->dx || second;
     const bool plain = bins <= kPlainSumsMaxBins;  // few enough bins per lane for plain block sums
     if (e == cudaSuccess && f32_plain) {
-        int64_t need = (a->n + kMlpBlock - 1) / kMlpBlock;
-        int64_t cap = (int64_t)sm_count() * 16;
-        int grid = (int)(need < cap ? need : cap);
+        // one CTA per tile: the block scheduler balances the SMs as CTAs finish
+        int grid = (int)((a->n + kMlpBlock - 1) / kMlpBlock);
         if (second) kv_plain_f32_kernel<true, true><<<grid, kMlpBlock, 0, s>>>(p, max_iter);
         else if (deriv && plain) kv_plain_f32_kernel<true, false, false><<<grid, kMlpBlock, 0, s>>>(p, max_iter);
         else if (deriv) kv_plain_f32_kernel<true><<<grid, kMlpBlock, 0, s>>>(p, max_iter);
