@@ -161,6 +161,35 @@ __device__ __forceinline__ float find_zero_f32(float v, float x, const BinsF& b,
     return a;
 }
 
+// Algorithm 2 in FP32 for both ends of the range at once: once the peak is known the t0 search on
+// [0, t_p] and the t1 search after FindRange are independent, so they run as the two components
+// of float2 iterates (x: t0, y: t1), each component taking exactly find_zero_f32's steps; the four
+// points of an iteration are evaluated as two pairs.  A pair whose t0 search is not needed runs it
+// on its placeholder end points (the result is not used), so that the warp runs one loop.
+__device__ __forceinline__ float2 find_zero2_f32(const BinsF& b, float le, float2 t_neg, float2 t_pos,
+                                                 float2 Fa, float2 dFa, int max_iter)
+{
+    float2 a = t_neg, bb = t_pos;
+    for (int i = 0; i < max_iter; ++i) {
+        const float2 shrink = fma2(fma2(a, f2(-1.0f), bb), f2(0.5f), a);
+        float2 newton = fma2(make_float2(-Fa.x, -Fa.y), make_float2(rcp_approx(dFa.x), rcp_approx(dFa.y)), a);
+        newton.x = isfinite(newton.x) ? newton.x : shrink.x;
+        newton.y = isfinite(newton.y) ? newton.y : shrink.y;
+        newton.x = fminf(fmaxf(newton.x, fminf(t_neg.x, shrink.x)), fmaxf(t_neg.x, shrink.x));
+        newton.y = fminf(fmaxf(newton.y, fminf(t_neg.y, shrink.y)), fmaxf(t_neg.y, shrink.y));
+        float2 F0, dF0, F1, dF1;  // (shrink, newton) of the t0 search, then of the t1 search
+        eval_F_f32x2<1>(0.0f, 0.0f, b, le, make_float2(shrink.x, newton.x), F0, dF0);
+        eval_F_f32x2<1>(0.0f, 0.0f, b, le, make_float2(shrink.y, newton.y), F1, dF1);
+        const bool s0 = F0.x < 0.0f, n0 = !s0 && F0.y < 0.0f;
+        const bool s1 = F1.x < 0.0f, n1 = !s1 && F1.y < 0.0f;
+        a = make_float2(s0 ? shrink.x : (n0 ? newton.x : a.x), s1 ? shrink.y : (n1 ? newton.y : a.y));
+        Fa = make_float2(s0 ? F0.x : (n0 ? F0.y : Fa.x), s1 ? F1.x : (n1 ? F1.y : Fa.y));
+        dFa = make_float2(s0 ? dF0.x : (n0 ? dF0.y : dFa.x), s1 ? dF1.x : (n1 ? dF1.y : dFa.y));
+        bb = make_float2(s0 ? bb.x : (n0 ? shrink.x : newton.x), s1 ? bb.y : (n1 ? shrink.y : newton.y));
+    }
+    return a;
+}
+
 // Algorithm 3's peak in FP32 (0 when v^2 <= x).
 __device__ __forceinline__ float peak_alg12_f32(float v, float x, int max_iter, bool& capped)
 {
@@ -177,13 +206,16 @@ __device__ __forceinline__ float peak_alg12_f32(float v, float x, int max_iter, 
 __device__ __forceinline__ bool range_alg12_f32(const BinsF& b, float tp, float le, int max_iter,
                                                 float& t0, float& t1, bool& capped)
 {
-    t0 = 0.0f;
     float h0, dh0;
     eval_h_f32(b, le, 0.0f, h0, dh0);
-    if (tp > 0.0f && h0 <= 0.0f) t0 = find_zero_f32<1>(0.0f, 0.0f, b, le, 0.0f, tp, h0, dh0, max_iter);
+    const bool left = tp > 0.0f && h0 <= 0.0f;  // the range does not reach t = 0
     float ts, te, F, dF;
     capped |= !find_range_f32<1>(0.0f, 0.0f, b, le, tp, ts, te, F, dF);
-    t1 = find_zero_f32<1>(0.0f, 0.0f, b, le, te, ts, F, dF, max_iter);
+    // t0 on [0, t_p] (negative end 0) and t1 on FindRange's bracket, together
+    const float2 r = find_zero2_f32(b, le, make_float2(0.0f, te), make_float2(left ? tp : 1.0f, ts),
+                                    make_float2(left ? h0 : -1.0f, F), make_float2(left ? dh0 : 1.0f, dF), max_iter);
+    t0 = left ? r.x : 0.0f;
+    t1 = r.y;
     return isfinite(t0) && isfinite(t1) && t0 >= 0.0f && t1 > t0;
 }
 
