@@ -470,19 +470,27 @@ __device__ __forceinline__ void bin_f32x2(const BinsF& b, const BinsK& k, float2
 // (2 + k) units of 2^-24 after k sequential additions — at most 13 units for up to 40 bins per
 // lane (10 blocks and one tail bin), 7.7e-7, so that a ratio of two sums stays within 1.6e-6.
 // The end weight 1/2 of bin 0 is applied to the first block's first term (lane 0 only); bin n
-// always falls in the tail loop, which selects its weight.  VOTE requires L = 1 and all 32 lanes
-// of the warp in the call with the same n.
+// falls in the tail loop, which selects its weight, unless the caller already has its terms
+// (with_end, L = 1 only: e0, e1, e2 are bin n's contributions to the three sums, which then start
+// from them).  VOTE requires L = 1 and all 32 lanes of the warp in the call with the same n.
 constexpr int kPlainSumsMaxBins = 40;
 
 template <int L, bool DERIV, bool VOTE = false, bool COMP = true>
-__device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, float& S1, float& S2)
+__device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, float& S1, float& S2,
+                                         bool with_end = false, float e0 = 0.0f, float e1 = 0.0f,
+                                         float e2 = 0.0f)
 {
     const BinsK k = bins_k(b);
     KahanSum<float> k0, k1, k2;
     k0.init();
     k1.init();
     k2.init();
-    float q0 = 0.0f, q1 = 0.0f, q2 = 0.0f;  // plain block sums (COMP = false)
+    if (!with_end) e0 = e1 = e2 = 0.0f;
+    k0.s = e0;
+    k1.s = e1;
+    k2.s = e2;
+    float q0 = e0, q1 = e1, q2 = e2;  // plain block sums (COMP = false)
+    const int last = with_end ? b.n - 1 : b.n;
     int m = lane;
     float mf = (float)lane;
     float c_first = lane == 0 ? 0.5f * k.kc : k.kc;
@@ -504,7 +512,7 @@ __device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, fl
             }
         }
     }
-    for (; m <= b.n; m += L, mf += (float)L) {
+    for (; m <= last; m += L, mf += (float)L) {
         float w, w1, w2;
         bin_f32<DERIV, VOTE>(b, k, mf, (m == 0 || m == b.n) ? 0.5f * k.kc : k.kc, w, w1, w2);
         if (COMP) k0.add(w); else q0 += w;

@@ -82,6 +82,16 @@ __device__ __forceinline__ df df_add_fast(df x, df y)
 
 __device__ __forceinline__ df df_sub_fast(df x, df y) { return df_add_fast(x, df_neg(y)); }
 
+// x + y and x - y as df_add_fast, for |x.hi| >= |y.hi| (FastTwoSum on the high parts).
+__device__ __forceinline__ df df_add_ordered(df x, df y)
+{
+    df s = fast_two_sum(x.hi, y.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ df df_sub_ordered(df x, df y) { return df_add_ordered(x, df_neg(y)); }
+
 // ln 2 as a float-float.
 __device__ __forceinline__ df df_ln2() { return df{0.6931472f, -1.9046542e-09f}; }
 

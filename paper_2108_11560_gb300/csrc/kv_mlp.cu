@@ -331,25 +331,41 @@ __device__ __forceinline__ PeakConst peak_constants(float v, float x, float tp, 
     // log1p(e^{-2u}) in [0, ln 2] from the approximate 2^x and log2 (absolute error ~2e-7)
     const float e2u = ex2_approx(-2.0f * LOG2E_F * u.hi);
     const float lu = lg2_approx(1.0f + e2u) * LN2_F;
-    const df ch = df_mul_f(df_add_fast(E, Ei), 0.5f * x);  // x cosh t_r
-    const df sh = df_mul_f(df_sub_fast(E, Ei), 0.5f * x);  // x sinh t_r
-    c.G = df_sub_fast(df_add_fast(df_add_fast(u, df_make(lu)), df_neg(df_ln2())), ch);
-    const df c1 = df_sub_fast(df_make(v), sh);
+    // e^{t_r} >= e^{-t_r}, so their high parts add and subtract exactly by FastTwoSum
+    const df shr = df_sub_ordered(E, Ei);                  // 2 sinh t_r
+    c.b.shp = 0.5f * (shr.hi + shr.lo);
+    const df ch = df_mul_f(df_add_ordered(E, Ei), 0.5f * x);  // x cosh t_r
+    const df sh = df_mul_f(shr, 0.5f * x);                 // x sinh t_r
+    // G = (u - x cosh t_r) + (lu - ln 2): the two large terms cancel, so their high parts are
+    // subtracted exactly (TwoSum) and everything else, at most a few units in size, is added
+    // in FP32 (absolute error a few 1e-8, below lu's own).  The pair is not normalised: the
+    // finish adds it to log(h S0) in that order (offset_plus).
+    const df d = two_sum(u.hi, -ch.hi);
+    c.G = df{d.hi, ((u.lo - ch.lo) + d.lo) + (lu - LN2_F)};
     c.b.v = v;
     c.b.u = u.hi;
     c.b.tp = tr.hi;
-    c.b.c1 = c1.hi + c1.lo;
+    // v - x sinh t_r: where the two are within a factor 2 of each other the first difference is
+    // exact, elsewhere there is no cancellation; either way one rounding of the result
+    c.b.c1 = (v - sh.hi) - sh.lo;
     c.b.ap = 0.5f * x * E.hi;
     c.b.am = 0.5f * x * Ei.hi;
     c.b.lu = lu;
     c.b.ep = E.hi;
     c.b.em = Ei.hi;
     c.b.e2u = e2u;
-    const df shr = df_sub_fast(E, Ei);  // 2 sinh t_r
-    c.b.shp = 0.5f * (shr.hi + shr.lo);
     c.b.xch = ch.hi + ch.lo;
     c.b.xsh = sh.hi + sh.lo;
     return c;
+}
+
+// log K = G + log(h S0) from the offset pair of peak_constants and y = log(h S0) in FP32: the
+// high part and y are added exactly (TwoSum), then the small rest, so the result is rounded once
+// (and carries y's own error, about 1e-7).
+__device__ __forceinline__ float offset_plus(const df& G, float y)
+{
+    const df s = two_sum(G.hi, y);
+    return s.hi + (s.lo + G.lo);
 }
 
 // The small per-unit weights of layers 1 and 3, passed by value with the launch so that the
@@ -413,60 +429,77 @@ __device__ __forceinline__ bool float_edge(float v, float x, float& lk, float& d
     return false;
 }
 
-// The check of a learned range: g - g(tr) at each end within [le - W, le] (le = log eps).  An
-// end that misses the window gets up to kNewtonSteps FP32 Newton steps towards the middle of the
-// window (the slope of the same cancellation-free difference) and must then pass the same check.
-// The left end becomes 0 when the range reaches t = 0.  Returns false when the pair must fall
-// back to the plain bracket.
+// The check of a learned range: g - g(tr) at each end within [le - W, le] (le = log eps).  Both
+// predicted ends are evaluated together (paired instructions), the left one clamped at t = 0,
+// where the range may start with the integrand still above the eps level (not too wide there
+// is all that is asked).  A left end inside (0, t_r) that passes leaves g(0) below the window
+// too, since g rises on [0, t_p].  Only the pairs that miss (about 1 % on the hard band) take the
+// slow part: an end outside the window gets up to kNewtonSteps FP32 Newton steps towards the
+// middle of the window (the slope of the same cancellation-free difference) and must then pass
+// the same check; the left end becomes 0 when the integrand at t = 0 is above the eps level.
+// Returns false when the pair must fall back to the plain bracket.  `end` receives the
+// trapezoid terms of bin n (t = t1, weight 1/2) from the right end's last evaluation, in the
+// units of the bins' sums: w = e^{g(t1) - g(t_r)} / 2, w t1 tanh(v t1) and -w x cosh(t1) log2 e.
+// At a passing end w <= e^{le} / 2, so the coarse evaluation's absolute error of about 1e-3 in
+// the exponent changes S0 by less than 1e-3 e^{le} of its peak term.
 constexpr int kNewtonSteps = 3;
+struct EndTerms {
+    float w, w1, w2;
+};
+
 __device__ __forceinline__ bool check_range(const BinsF& b, float tr, float w0, float w1, float le,
-                                            float lo, float& t0, float& t1)
+                                            float lo, float& t0, float& t1, EndTerms& end)
 {
     const float mid = le - 0.5f * (float)kWindow;
     auto in_window = [&](float d) { return d <= le && d >= lo; };
-    float e2, es, ems;
     float s1 = w1;
-    float d1 = delta_g_coarse(b, s1, e2, es, ems);
-    for (int k = 0; k < kNewtonSteps && !in_window(d1); ++k) {
-        const float slope = delta_g_slope_f32(b, e2, es, ems);
-        float sn = s1 - (d1 - mid) / slope;
-        if (!(slope < 0.0f) || !isfinite(sn)) sn = d1 > le ? 2.0f * s1 : 0.5f * s1;
-        s1 = fminf(fmaxf(sn, 0.25f * s1), 4.0f * s1);
-        d1 = delta_g_coarse(b, s1, e2, es, ems);
-    }
-    bool ok = in_window(d1);
-    t1 = tr + s1;
-    t0 = 0.0f;
-    if (tr > 0.0f) {
-        // the left end: the predicted one, or 0 when the range reaches it
-        float s0 = -fminf(w0, tr);
-        // at t = 0 and at the predicted left end, together
-        float2 e2p, esp, emsp;
-        const float2 dzp = delta_g_coarse2(b, make_float2(-tr, s0), e2p, esp, emsp);
-        const float dz = dzp.x;
-        if (dz > le || (s0 <= -tr && dz >= lo)) {
-            t0 = 0.0f;  // the range starts at 0 and is not too wide there
-        } else {
-            float d0 = s0 <= -tr ? dz : dzp.y;
-            e2 = e2p.y;
-            es = esp.y;
-            ems = emsp.y;
-            for (int k = 0; k < kNewtonSteps && !in_window(d0) && s0 > -tr; ++k) {
-                const float slope = delta_g_slope_f32(b, e2, es, ems);
-                float sn = s0 - (d0 - mid) / slope;
-                if (!(slope > 0.0f) || !isfinite(sn)) sn = d0 > le ? 2.0f * s0 : 0.5f * s0;
-                s0 = fmaxf(fminf(sn, 0.25f * s0), 4.0f * s0);
-                if (s0 <= -tr) {
-                    s0 = -tr;
-                    d0 = dz;
-                } else {
-                    d0 = delta_g_coarse(b, s0, e2, es, ems);
-                }
-            }
-            ok = ok && (in_window(d0) || (s0 <= -tr && d0 >= lo));
-            t0 = fmaxf(tr + s0, 0.0f);
+    float s0 = -fminf(w0, tr);  // s0 = -t_r: the left end is t = 0
+    float2 e2p, esp, emsp;
+    const float2 dp = delta_g_coarse2(b, make_float2(s1, s0), e2p, esp, emsp);
+    float d1 = dp.x, e21 = e2p.x, es1 = esp.x, ems1 = emsp.x;
+    const bool at0 = s0 <= -tr;
+    const bool ok0 = at0 ? dp.y >= lo : in_window(dp.y);
+    bool ok = in_window(d1) && ok0;
+    if (!ok) {
+        for (int k = 0; k < kNewtonSteps && !in_window(d1); ++k) {
+            const float slope = delta_g_slope_f32(b, e21, es1, ems1);
+            float sn = s1 - (d1 - mid) / slope;
+            if (!(slope < 0.0f) || !isfinite(sn)) sn = d1 > le ? 2.0f * s1 : 0.5f * s1;
+            s1 = fminf(fmaxf(sn, 0.25f * s1), 4.0f * s1);
+            d1 = delta_g_coarse(b, s1, e21, es1, ems1);
         }
+        bool okl = ok0;
+        if (!ok0) {
+            float e2, es, ems;
+            const float dz = at0 ? dp.y : delta_g_coarse(b, -tr, e2, es, ems);
+            if (dz > le) {
+                s0 = -tr;  // the range starts at 0, where the integrand is above the eps level
+                okl = true;
+            } else if (!at0) {
+                float d0 = delta_g_coarse(b, s0, e2, es, ems);  // again, for the slope's inputs
+                for (int k = 0; k < kNewtonSteps && !in_window(d0) && s0 > -tr; ++k) {
+                    const float slope = delta_g_slope_f32(b, e2, es, ems);
+                    float sn = s0 - (d0 - mid) / slope;
+                    if (!(slope > 0.0f) || !isfinite(sn)) sn = d0 > le ? 2.0f * s0 : 0.5f * s0;
+                    s0 = fmaxf(fminf(sn, 0.25f * s0), 4.0f * s0);
+                    if (s0 <= -tr) {
+                        s0 = -tr;
+                        d0 = dz;
+                    } else {
+                        d0 = delta_g_coarse(b, s0, e2, es, ems);
+                    }
+                }
+                okl = in_window(d0) || (s0 <= -tr && d0 >= lo);
+            }
+        }
+        ok = in_window(d1) && okl;
     }
+    t1 = tr + s1;
+    t0 = fmaxf(tr + s0, 0.0f);
+    const float we = 0.5f * ex2_approx(d1 * LOG2E_F);
+    end.w = we;
+    end.w1 = we * (t1 * ((1.0f - e21) * rcp_approx(1.0f + e21)));
+    end.w2 = (we * -LOG2E_F) * fmaf(b.ap, es1, b.am * ems1);
     return ok;
 }
 
@@ -561,10 +594,14 @@ constexpr uint32_t kTmemCols = 64;
 // the same straight-line code into the bins.  Then FP32 bins, the finish with the float-float
 // offset, and the stores.  An edge pair's results are taken from (v, x) again after the bins, so
 // that they hold no registers during them.
+// `end`: bin n's terms from the range check (check_range), used while log eps <= kEndTermLogEps,
+// where their coarse exponent cannot matter; otherwise bin n is one of the bins.
+constexpr float kEndTermLogEps = -12.0f;
+
 template <bool DERIV, bool D2, bool COMP = true>
 __device__ __forceinline__ void pair_tail(const MlpPathParams& p, int64_t i, bool active, bool edge, bool ok,
                                           float v, float x, PeakConst& c, float t0, float t1,
-                                          uint8_t ok_status = KV_PAIR_OK)
+                                          uint8_t ok_status = KV_PAIR_OK, const EndTerms* end = nullptr)
 {
     const float tr = c.b.tp;
     const bool regular = active && !edge;
@@ -596,18 +633,27 @@ __device__ __forceinline__ void pair_tail(const MlpPathParams& p, int64_t i, boo
         if (v < 0.0f) dvx = -dvx;
         if (edge) d2v = dvx = d2x = (isinf(x) && x > 0.0f) ? 0.0f : nanf("");
     } else {
-        sums_f32<1, DERIV, true, COMP>(c.b, 0, S0, S1, S2);
+        if (end)
+            sums_f32<1, DERIV, true, COMP>(c.b, 0, S0, S1, S2, p.log_eps <= kEndTermLogEps, end->w, end->w1, end->w2);
+        else
+            sums_f32<1, DERIV, true, COMP>(c.b, 0, S0, S1, S2);
     }
-    float lk, dv, dx;
-    float_edge(v, x, lk, dv, dx);
+    float lk = 0.0f, dv = 0.0f, dx = 0.0f;
     if (regular && ok) {
         // log(h S0) from the approximate log2 (absolute error about 1e-7)
-        df L = df_add(c.G, df_make(lg2_approx(c.b.h * S0) * LN2_F));
-        lk = L.hi + L.lo;
+        lk = offset_plus(c.G, lg2_approx(c.b.h * S0) * LN2_F);
         const float r = rcp_approx(S0);
         dv = DERIV ? copysignf(S1 * r, v) : 0.0f;
         if (v == 0.0f) dv = 0.0f;
         dx = DERIV ? -(S2 * r) : 0.0f;
+    }
+    if (__any_sync(0xffffffffu, edge)) {  // edge pairs are rare: only their warps take this
+        float le, de, xe;
+        if (float_edge(v, x, le, de, xe)) {
+            lk = le;
+            dv = de;
+            dx = xe;
+        }
     }
     if (active && (edge || ok)) {
         if (p.go) {
@@ -786,8 +832,9 @@ __global__ void __launch_bounds__(kMlpBlock, D2 ? 6 : 8) kv_mlp_tc_kernel(MlpPat
         const float w0 = fmaxf(fmaxf(__expf(L0) - DELTA, 0.0f) - (tp - tr), 0.0f);
         const float w1 = fmaxf(fmaxf(__expf(L1) - DELTA, 0.0f) + (tp - tr), 1e-6f * (1.0f + tr));
         float t0, t1;
-        const bool ok = check_range(c.b, tr, w0, w1, p.log_eps, lo_ok, t0, t1);
-        pair_tail<DERIV, D2, COMP>(p, i, active, edge, ok, v, x, c, t0, t1);
+        EndTerms et;
+        const bool ok = check_range(c.b, tr, w0, w1, p.log_eps, lo_ok, t0, t1, et);
+        pair_tail<DERIV, D2, COMP>(p, i, active, edge, ok, v, x, c, t0, t1, KV_PAIR_OK, D2 ? nullptr : &et);
     }
     if (aborted) {
         // a tensor-core wait ran out: this tile, the one claimed for the next trip and every tile
@@ -920,7 +967,7 @@ __global__ void __launch_bounds__(kMlpBlock) kv_fallback_kernel(FallbackParams f
                 } else {
                     sums_f32<1, DERIV>(c.b, 0, S0, S1, S2);
                 }
-                df L = df_add(c.G, df_make(lg2_approx(c.b.h * S0) * LN2_F));
+                const float lkf = offset_plus(c.G, lg2_approx(c.b.h * S0) * LN2_F);
                 const float r = rcp_approx(S0);
                 float dv = DERIV ? copysignf(S1 * r, vf) : 0.0f;
                 if (vf == 0.0f) dv = 0.0f;
@@ -929,7 +976,7 @@ __global__ void __launch_bounds__(kMlpBlock) kv_fallback_kernel(FallbackParams f
                     dv *= p.go[i];
                     dx *= p.go[i];
                 }
-                if (p.logk) p.logk[i] = L.hi + L.lo;
+                if (p.logk) p.logk[i] = lkf;
                 if (p.dv) p.dv[i] = dv;
                 if (p.dx) p.dx[i] = dx;
                 if (p.status) p.status[i] = KV_PAIR_FALLBACK | (capped ? KV_PAIR_RANGE_CAP : 0);
