@@ -18,6 +18,7 @@
 // The per-pair constants (v - x sinh t_p, x e^{+-t_p}/2, log1p(e^{-2u}), g(t_p)) carry extra
 // precision: FP64 with the plain bracket, float-float with the learned one.
 #pragma once
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -400,11 +401,13 @@ constexpr float TANH_SERIES_MAX = 0.35f;
 constexpr float EA_SERIES_MIN = -2.0f * LOG2E_F * TANH_SERIES_MAX;
 
 // One FP32 bin at m = mf (a float holding a small integer, exact): its weight c e^{g(t_m) - g(t_p)}
-// and the two derivative integrands' weights.  `ck` is c e^{-lu}.  With VOTE (all 32 lanes of the
-// warp run the same bins together) the series for tanh(vt) is evaluated only when some lane of
-// the warp needs it.
+// and the two derivative integrands' weights, all divided by e^{-lu} (the sums apply that factor
+// once): wp = c 2^{c1 s + N(s)}, w = wp (1 + e^{-2vt}) and w tanh(vt) = wp (1 - e^{-2vt}), the
+// latter as one fused multiply-add (the product rounded once).  `c` is the trapezoid factor
+// (1/2 at the ends, else 1).  With VOTE (all 32 lanes of the warp run the same bins together)
+// the series for tanh(vt) is evaluated only when some lane of the warp needs it.
 template <bool DERIV, bool VOTE>
-__device__ __forceinline__ void bin_f32(const BinsF& b, const BinsK& k, float mf, float ck, float& w,
+__device__ __forceinline__ void bin_f32(const BinsF& b, const BinsK& k, float mf, float c, float& w,
                                         float& w1, float& w2)
 {
     const float s = fmaf(mf, b.h, b.s0);
@@ -412,16 +415,15 @@ __device__ __forceinline__ void bin_f32(const BinsF& b, const BinsK& k, float mf
     const float N = x_part<DERIV>(k, s, nxc);
     const float ea = fmaf(k.nv2, s, k.nu2);
     const float e2 = ex2_approx(ea);  // e^{-2vt}
-    const float ope = 1.0f + e2;
-    const float wp = ck * ex2_approx(fmaf(k.c1, s, N));
-    w = wp * ope;
+    const float wp = c * ex2_approx(fmaf(k.c1, s, N));
+    w = fmaf(wp, e2, wp);
     if (DERIV) {
         const float t = b.tp + s;
-        float q = 1.0f - e2;  // (1 + e^{-2vt}) tanh(vt)
+        float d = fmaf(wp, -e2, wp);  // w tanh(vt)
         const bool small = ea > EA_SERIES_MIN;
         if (!VOTE || __any_sync(0xffffffffu, small))
-            q = small ? tanh_small(ea * (-0.5f * LN2_F)) * ope : q;
-        w1 = wp * (t * q);
+            d = small ? w * tanh_small(ea * (-0.5f * LN2_F)) : d;
+        w1 = t * d;
         w2 = w * nxc;  // w cosh t times -x log2 e
     }
 }
@@ -436,9 +438,10 @@ __device__ __forceinline__ float2 tanh_small2(float2 y)
     return fma2(mul2(y, z), p, y);
 }
 
-// bin_f32 for the two bins m = mf.x and mf.y; ck.x and ck.y are their factors c e^{-lu}.
-template <bool DERIV, bool VOTE>
-__device__ __forceinline__ void bin_f32x2(const BinsF& b, const BinsK& k, float2 mf, float2 ck, float2& w,
+// bin_f32 for the two bins m = mf.x and mf.y; with CK their trapezoid factors are c.x and c.y,
+// without they are 1 (no multiplication).
+template <bool DERIV, bool VOTE, bool CK>
+__device__ __forceinline__ void bin_f32x2(const BinsF& b, const BinsK& k, float2 mf, float2 c, float2& w,
                                           float2& w1, float2& w2)
 {
     const float2 s = fma2(mf, f2(b.h), f2(b.s0));
@@ -446,19 +449,19 @@ __device__ __forceinline__ void bin_f32x2(const BinsF& b, const BinsK& k, float2
     const float2 N = x_part2<DERIV>(k, s, nxc);
     const float2 ea = fma2(f2(k.nv2), s, f2(k.nu2));
     const float2 e2 = make_float2(ex2_approx(ea.x), ex2_approx(ea.y));  // e^{-2vt}
-    const float2 ope = add2(f2(1.0f), e2);
     const float2 dg = fma2(f2(k.c1), s, N);
-    const float2 wp = mul2(ck, make_float2(ex2_approx(dg.x), ex2_approx(dg.y)));
-    w = mul2(wp, ope);
+    float2 wp = make_float2(ex2_approx(dg.x), ex2_approx(dg.y));
+    if constexpr (CK) wp = mul2(c, wp);
+    w = fma2(wp, e2, wp);
     if (DERIV) {
         const float2 t = add2(f2(b.tp), s);
-        float2 q = sub2(f2(1.0f), e2);  // (1 + e^{-2vt}) tanh(vt)
+        float2 d = fma2(wp, make_float2(-e2.x, -e2.y), wp);  // w tanh(vt)
         const bool kx = ea.x > EA_SERIES_MIN, ky = ea.y > EA_SERIES_MIN;
         if (!VOTE || __any_sync(0xffffffffu, kx || ky)) {
-            const float2 tq = mul2(tanh_small2(mul2(ea, f2(-0.5f * LN2_F))), ope);  // vt from ea
-            q = make_float2(kx ? tq.x : q.x, ky ? tq.y : q.y);
+            const float2 wt = mul2(w, tanh_small2(mul2(ea, f2(-0.5f * LN2_F))));  // vt from ea
+            d = make_float2(kx ? wt.x : d.x, ky ? wt.y : d.y);
         }
-        w1 = mul2(wp, mul2(t, q));
+        w1 = mul2(t, d);
         w2 = mul2(w, nxc);  // w cosh t times -x log2 e
     }
 }
@@ -485,20 +488,25 @@ __device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, fl
     k0.init();
     k1.init();
     k2.init();
-    if (!with_end) e0 = e1 = e2 = 0.0f;
-    k0.s = e0;
-    k1.s = e1;
-    k2.s = e2;
-    float q0 = e0, q1 = e1, q2 = e2;  // plain block sums (COMP = false)
+    // the bins' terms leave out the factor e^{-lu} = 1 / (1 + e^{-2u}), applied to the sums at
+    // the end; bin n's terms from the caller include it
+    if (with_end) {
+        const float rkc = 1.0f + b.e2u;
+        k0.s = e0 * rkc;
+        k1.s = e1 * rkc;
+        k2.s = e2 * rkc;
+    }
+    float q0 = k0.s, q1 = k1.s, q2 = k2.s;  // plain block sums (COMP = false)
     const int last = with_end ? b.n - 1 : b.n;
     int m = lane;
     float mf = (float)lane;
-    float c_first = lane == 0 ? 0.5f * k.kc : k.kc;
-    for (; m + 3 * L < b.n; m += 4 * L, mf += (float)(4 * L)) {
+    // the first block carries bin 0's factor 1/2 (lane 0); the later ones multiply by nothing
+    auto block = [&](auto ck) {
+        constexpr bool CK = decltype(ck)::value;
         float2 wa, w1a, w2a, wb, w1b, w2b;
-        bin_f32x2<DERIV, VOTE>(b, k, make_float2(mf, mf + (float)L), make_float2(c_first, k.kc), wa, w1a, w2a);
-        bin_f32x2<DERIV, VOTE>(b, k, make_float2(mf + (float)(2 * L), mf + (float)(3 * L)), f2(k.kc), wb, w1b, w2b);
-        c_first = k.kc;
+        bin_f32x2<DERIV, VOTE, CK>(b, k, make_float2(mf, mf + (float)L), make_float2(lane == 0 ? 0.5f : 1.0f, 1.0f),
+                                   wa, w1a, w2a);
+        bin_f32x2<DERIV, VOTE, false>(b, k, make_float2(mf + (float)(2 * L), mf + (float)(3 * L)), f2(1.0f), wb, w1b, w2b);
         const float2 p0 = add2(wa, wb);
         if (COMP) k0.add(p0.x + p0.y); else q0 += p0.x + p0.y;
         if (DERIV) {
@@ -511,10 +519,16 @@ __device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, fl
                 q2 += p2.x + p2.y;
             }
         }
+    };
+    if (m + 3 * L < b.n) {
+        block(std::true_type());
+        m += 4 * L;
+        mf += (float)(4 * L);
     }
+    for (; m + 3 * L < b.n; m += 4 * L, mf += (float)(4 * L)) block(std::false_type());
     for (; m <= last; m += L, mf += (float)L) {
         float w, w1, w2;
-        bin_f32<DERIV, VOTE>(b, k, mf, (m == 0 || m == b.n) ? 0.5f * k.kc : k.kc, w, w1, w2);
+        bin_f32<DERIV, VOTE>(b, k, mf, (m == 0 || m == b.n) ? 0.5f : 1.0f, w, w1, w2);
         if (COMP) k0.add(w); else q0 += w;
         if (DERIV) {
             if (COMP) {
@@ -531,9 +545,9 @@ __device__ __forceinline__ void sums_f32(const BinsF& b, int lane, float& S0, fl
         k1.s = q1;
         k2.s = q2;
     }
-    S0 = lane_sum<float, L>(k0.value());
-    S1 = DERIV ? lane_sum<float, L>(k1.value()) : 0.0f;
-    S2 = DERIV ? lane_sum<float, L>(k2.value()) * k.s2 : 0.0f;
+    S0 = lane_sum<float, L>(k0.value()) * k.kc;
+    S1 = DERIV ? lane_sum<float, L>(k1.value()) * k.kc : 0.0f;
+    S2 = DERIV ? lane_sum<float, L>(k2.value()) * (k.s2 * k.kc) : 0.0f;
 }
 
 // ------------------------------------------------------------------ second derivatives
