@@ -430,18 +430,21 @@ __device__ __forceinline__ bool float_edge(float v, float x, float& lk, float& d
 }
 
 // The check of a learned range: g - g(tr) at each end within [le - W, le] (le = log eps).  Both
-// predicted ends are evaluated together (paired instructions), the left one clamped at t = 0,
-// where the range may start with the integrand still above the eps level (not too wide there
-// is all that is asked).  A left end inside (0, t_r) that passes leaves g(0) below the window
-// too, since g rises on [0, t_p].  Only the pairs that miss (about 1 % on the hard band) take the
-// slow part: an end outside the window gets up to kNewtonSteps FP32 Newton steps towards the
-// middle of the window (the slope of the same cancellation-free difference) and must then pass
-// the same check; the left end becomes 0 when the integrand at t = 0 is above the eps level.
-// Returns false when the pair must fall back to the plain bracket.  `end` receives the
-// trapezoid terms of bin n (t = t1, weight 1/2) from the right end's last evaluation, in the
-// units of the bins' sums: w = e^{g(t1) - g(t_r)} / 2, w t1 tanh(v t1) and -w x cosh(t1) log2 e.
-// At a passing end w <= e^{le} / 2, so the coarse evaluation's absolute error of about 1e-3 in
-// the exponent changes S0 by less than 1e-3 e^{le} of its peak term.
+// ends are evaluated together (paired instructions).  The left one is taken at t = 0 when the
+// prediction puts it within the last kLeftZeroFrac of [0, t_r] (where the network cannot tell a
+// range that starts at 0 from one that nearly does): a range may start at 0 with the integrand
+// there anywhere above le - W (not too wide is all that is asked); otherwise the predicted end
+// must lie inside the window, and then g(0) is below it too, since g rises on [0, t_p].  Only
+// the pairs that miss take the slow part: a right end outside the window gets up to
+// kNewtonSteps FP32 Newton steps towards the middle of the window (the slope of the same
+// cancellation-free difference); a left end that missed starts at 0 if the integrand there is
+// above le - W, else gets the same Newton steps from the predicted end.  Returns false when the
+// pair must fall back to the plain bracket.  `end` receives the trapezoid terms of bin n
+// (t = t1, weight 1/2) from the right end's last evaluation, in the units of the bins' sums:
+// w = e^{g(t1) - g(t_r)} / 2, w t1 tanh(v t1) and -w x cosh(t1) log2 e.  At a passing end
+// w <= e^{le} / 2, so the coarse evaluation's absolute error of about 1e-3 in the exponent
+// changes S0 by less than 1e-3 e^{le} of its peak term.
+constexpr float kLeftZeroFrac = 0.9f;
 constexpr int kNewtonSteps = 3;
 struct EndTerms {
     float w, w1, w2;
@@ -453,17 +456,18 @@ __device__ __forceinline__ bool check_range(const BinsF& b, float tr, float w0, 
     const float mid = le - 0.5f * (float)kWindow;
     auto in_window = [&](float d) { return d <= le && d >= lo; };
     float s1 = w1;
-    float s0 = -fminf(w0, tr);  // s0 = -t_r: the left end is t = 0
+    const float s0p = -fminf(w0, tr);                     // the predicted left end
+    const bool at0 = w0 >= kLeftZeroFrac * tr;            // take the left end at t = 0
+    float s0 = at0 ? -tr : s0p;
     float2 e2p, esp, emsp;
     const float2 dp = delta_g_coarse2(b, make_float2(s1, s0), e2p, esp, emsp);
     float d1 = dp.x, e21 = e2p.x, es1 = esp.x, ems1 = emsp.x;
-    const bool at0 = s0 <= -tr;
     const bool ok0 = at0 ? dp.y >= lo : in_window(dp.y);
     bool ok = in_window(d1) && ok0;
     if (!ok) {
         for (int k = 0; k < kNewtonSteps && !in_window(d1); ++k) {
             const float slope = delta_g_slope_f32(b, e21, es1, ems1);
-            float sn = s1 - (d1 - mid) / slope;
+            float sn = s1 - __fdividef(d1 - mid, slope);
             if (!(slope < 0.0f) || !isfinite(sn)) sn = d1 > le ? 2.0f * s1 : 0.5f * s1;
             s1 = fminf(fmaxf(sn, 0.25f * s1), 4.0f * s1);
             d1 = delta_g_coarse(b, s1, e21, es1, ems1);
@@ -472,14 +476,15 @@ __device__ __forceinline__ bool check_range(const BinsF& b, float tr, float w0, 
         if (!ok0) {
             float e2, es, ems;
             const float dz = at0 ? dp.y : delta_g_coarse(b, -tr, e2, es, ems);
-            if (dz > le) {
-                s0 = -tr;  // the range starts at 0, where the integrand is above the eps level
+            if (dz >= lo) {
+                s0 = -tr;  // the range starts at 0, where the integrand is not too small
                 okl = true;
-            } else if (!at0) {
+            } else if (s0p > -tr) {
+                s0 = s0p;
                 float d0 = delta_g_coarse(b, s0, e2, es, ems);  // again, for the slope's inputs
                 for (int k = 0; k < kNewtonSteps && !in_window(d0) && s0 > -tr; ++k) {
                     const float slope = delta_g_slope_f32(b, e2, es, ems);
-                    float sn = s0 - (d0 - mid) / slope;
+                    float sn = s0 - __fdividef(d0 - mid, slope);
                     if (!(slope > 0.0f) || !isfinite(sn)) sn = d0 > le ? 2.0f * s0 : 0.5f * s0;
                     s0 = fmaxf(fminf(sn, 0.25f * s0), 4.0f * s0);
                     if (s0 <= -tr) {
