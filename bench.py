@@ -67,41 +67,49 @@ F64_SLICE = 1 << 23     # the FP64 path's slice of the workload (134 MB of float
 
 # Algorithmic FP32 work of the learned-bracket fast path, counted operation by operation from
 # its formulas with an FMA as one operation and a paired (f32x2) instruction as two:
-#   per bin: the abscissa 1, the exponent's x-part (the phi polynomials, or x cosh t from e^{+-s},
-#            which the d/dx integrand shares) 16, the rest of the weight 5, the two derivative
-#            integrands 5 (+ the tanh polynomial in the ~33 % of warp-blocks that need it, ~2.7),
-#            three sums 3 (plain block sums) or 5.25 (compensated)     -> 32.7 or 35 (+ 4 MUFU)
+#   per bin (bins 0..n-1; bin n's terms come from the range check): the abscissa 1, the
+#            exponent's x-part (the phi polynomials, or x cosh t from e^{+-s}, which the d/dx
+#            integrand shares) 16, the rest of the weight 2, the two derivative integrands 4
+#            (+ the tanh polynomial in the warp-blocks that need it, ~3), three sums 3 (plain
+#            block sums) or 5.25 (compensated)                             -> ~29.6 or ~32 (+ 4 MUFU)
 #   per pair: layer 1 and layer 3 on the CUDA cores 256 (layer 2 runs on the tensor cores and
-#             is not counted), one peak Newton step, offset constants, endpoint check, setup and
-#             finish ~225                                                       -> 482
+#             is not counted), one peak Newton step, offset constants, endpoint check with bin
+#             n's terms, setup and finish ~190                                    -> ~446
 # ncu's executed FFMA + FADD + FMUL (+ 2 x FFMA2/FADD2/FMUL2) counters over 4M hard-band pairs (one
 # launch of the fast-path kernel each) give these per bin and per pair: for the kernel instance
-# with plain block sums (up to PLAIN_SUMS_MAX_BINS bins), from launches at 1 and 32 bins; for the
-# instance with compensated block sums (more bins), from launches at 41 and 64 bins.
+# with plain block sums (up to PLAIN_SUMS_MAX_BINS bins), from launches at 8 and 32 bins; for the
+# instance with compensated block sums (more bins), from launches at 44 and 64 bins.
 PLAIN_SUMS_MAX_BINS = 40
-FP32_OPS_PER_BIN = 32.886
-FP32_OPS_PER_PAIR = 482.27
-FP32_OPS_PER_BIN_COMP = 34.703
-FP32_OPS_PER_PAIR_COMP = 512.27
+FP32_OPS_PER_BIN = 29.606
+FP32_OPS_PER_PAIR = 446.32
+FP32_OPS_PER_BIN_COMP = 31.886
+FP32_OPS_PER_PAIR_COMP = 445.46
 MUFU_OPS_PER_BIN = 4
 # XU-pipe (MUFU) operations per pair outside the bins from the same captures
-# (smsp__inst_executed_pipe_xu x 32: 43.2 per pair at 1 bin, 4.0 per bin), and the XU pipe's lanes
-# per SM per clock that ncu's XU percentages are taken against (167.2 operations per pair in
-# 0.280 ms per 4M pairs read as 27 percent of the active cycles there).
-MUFU_OPS_PER_PAIR = 35.18
+# (smsp__inst_executed_pipe_xu x 32: 33.56 per pair and 4.0 per bin), and the XU pipe's lanes
+# per SM per clock that ncu's XU percentages are taken against.
+MUFU_OPS_PER_PAIR = 33.56
 XU_LANES_PER_SM = 32
+# Warp instructions issued per pair (smsp__inst_executed x 32 / pairs, same captures): the fast
+# path is bound by instruction issue (one warp instruction per SM sub-partition per clock) as
+# much as by the FP32 pipe, so the line also reports issue-slot utilisation.
+INST_PER_BIN = 26.618
+INST_PER_PAIR = 861.3
+INST_PER_BIN_COMP = 29.642
+INST_PER_PAIR_COMP = 861.6
+ISSUE_PER_SM = 4
 # DRAM bytes per pair of the fast-path kernel (read + write) from an ncu capture of one full
 # 16,777,216-pair launch at 32 bins in steady state (the fourth of five consecutive launches, no
 # cache flush between them, so the previous launch's outputs are written back inside it):
-# 201.43 MB read + 198.81 MB written.  The algorithmic bytes per pair are v, x, grad_out in and
+# 201.42 MB read + 198.86 MB written.  The algorithmic bytes per pair are v, x, grad_out in and
 # log K, d/dv, d/dx out, 4 bytes each (402.65 MB per launch).
-TRAFFIC_BYTES_PER_PAIR = (201.43e6 + 198.81e6) / 16777216
+TRAFFIC_BYTES_PER_PAIR = (201.41568e6 + 198.8608e6) / 16777216
 ALGORITHMIC_BYTES_PER_PAIR = 24
 # The counts above hold for the fast-path kernel built from these sources; COUNTS_SOURCE_SHA is
 # their hash when the counts were taken.  When the sources change, the line says so and reports
 # no traffic until the counters are taken again.
 COUNTS_SOURCES = ("kv_mlp.cu", "kv_bins.cuh", "kv_dfloat.cuh")
-COUNTS_SOURCE_SHA = "a36ed0da5394154a"
+COUNTS_SOURCE_SHA = "6b90f7f1722eb2cd"
 
 PATHS = {
     # name: (bracket, second derivatives, float64 I/O)
@@ -240,7 +248,7 @@ def run_reference(args):
 def sfu_utilisation(n_pairs, bins, launch_ms, sms, sm_mhz):
     """XU (MUFU: ex2, lg2, rcp) operations per second of the fast-path kernel against the XU
     pipe's peak, the second half of the metric's "% of FP32/SFU peak"."""
-    ops = n_pairs * (MUFU_OPS_PER_PAIR + (bins + 1) * MUFU_OPS_PER_BIN)
+    ops = n_pairs * (MUFU_OPS_PER_PAIR + bins * MUFU_OPS_PER_BIN)
     achieved = ops / (launch_ms / 1e3)
     peak = sms * XU_LANES_PER_SM * sm_mhz * 1e6
     return {"achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "T XU ops/s",
@@ -252,8 +260,20 @@ def sfu_utilisation(n_pairs, bins, launch_ms, sms, sm_mhz):
 def fp32_ops(bins):
     """FP32 operations per pair of the fast-path kernel instance that runs at this bin count."""
     if bins <= PLAIN_SUMS_MAX_BINS:
-        return FP32_OPS_PER_PAIR + (bins + 1) * FP32_OPS_PER_BIN
-    return FP32_OPS_PER_PAIR_COMP + (bins + 1) * FP32_OPS_PER_BIN_COMP
+        return FP32_OPS_PER_PAIR + bins * FP32_OPS_PER_BIN
+    return FP32_OPS_PER_PAIR_COMP + bins * FP32_OPS_PER_BIN_COMP
+
+
+def issue_utilisation(n_pairs, bins, launch_ms, sms, sm_mhz):
+    """Warp instructions issued per second by the fast-path kernel against the SMs' issue rate
+    (one warp instruction per sub-partition per clock)."""
+    per_pair = (INST_PER_PAIR + bins * INST_PER_BIN if bins <= PLAIN_SUMS_MAX_BINS
+                else INST_PER_PAIR_COMP + bins * INST_PER_BIN_COMP)
+    achieved = n_pairs * per_pair / 32 / (launch_ms / 1e3)
+    peak = sms * ISSUE_PER_SM * sm_mhz * 1e6
+    return {"achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "T warp instructions/s",
+            "frac": achieved / peak, "inst_per_pair": per_pair,
+            "peak_source": f"{sms} SMs x {ISSUE_PER_SM} sub-partitions x {sm_mhz:.0f} MHz"}
 
 
 def fp32_roofline(n_pairs, bins, launch_ms, sms, sm_mhz, peak_src):
@@ -659,6 +679,7 @@ def main():
     counts_current = sha == COUNTS_SOURCE_SHA
     roofline = None
     sfu = None
+    issue = None
     if bracket == "mlp" and not second:
         # the step's two launches: the fast-path kernel is > 99.8 % of the GPU time (ncu launch
         # list of this command), so its launch time is taken as the step time
@@ -671,6 +692,8 @@ def main():
         roofline["counts_current"] = counts_current
         sfu = sfu_utilisation(n_pairs, args.bins, launch_ms, sms, sm_mhz)
         sfu["counts_current"] = counts_current
+        issue = issue_utilisation(n_pairs, args.bins, launch_ms, sms, sm_mhz)
+        issue["counts_current"] = counts_current
     io_desc = "float64" if f64io else "float32"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -687,6 +710,7 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "sfu": sfu,
+        "issue": issue,
         "accuracy": acc,
         "e2e": e2e,
         "gpu_launches": int(launches),

@@ -14,14 +14,19 @@ def test_bench_module_imports_and_defines_counts():
 
     assert bench.FP32_OPS_PER_BIN > 0 and bench.FP32_OPS_PER_PAIR > 0
     # the instance with plain block sums below the threshold, compensated sums above it
-    assert bench.fp32_ops(bench.PLAIN_SUMS_MAX_BINS) == bench.FP32_OPS_PER_PAIR + (bench.PLAIN_SUMS_MAX_BINS + 1) * bench.FP32_OPS_PER_BIN
-    assert bench.fp32_ops(64) == bench.FP32_OPS_PER_PAIR_COMP + 65 * bench.FP32_OPS_PER_BIN_COMP
+    # bins 0..n-1 run in the bin loop (bin n's terms come from the range check)
+    assert bench.fp32_ops(bench.PLAIN_SUMS_MAX_BINS) == bench.FP32_OPS_PER_PAIR + bench.PLAIN_SUMS_MAX_BINS * bench.FP32_OPS_PER_BIN
+    assert bench.fp32_ops(64) == bench.FP32_OPS_PER_PAIR_COMP + 64 * bench.FP32_OPS_PER_BIN_COMP
     assert callable(bench._env_rank) and callable(bench.all_reduce_scalar)
-    # the SFU figure of the 16.7M-pair step at 32 bins, 1.273 ms, 152 SMs at 2070 MHz
-    s = bench.sfu_utilisation(16_777_216, 32, 1.273, 152, 2070.0)
+    # the SFU figure of a 16.7M-pair step at 32 bins, 0.967 ms, 152 SMs at 2070 MHz
+    s = bench.sfu_utilisation(16_777_216, 32, 0.967, 152, 2070.0)
     assert set(s) >= {"achieved", "peak", "unit", "frac", "peak_source"}
     assert abs(s["peak"] - 152 * 32 * 2070e6 / 1e12) < 1e-9
-    assert 0.2 < s["frac"] < 0.25 and abs(s["frac"] - s["achieved"] / s["peak"]) < 1e-12
+    assert 0.2 < s["frac"] < 0.35 and abs(s["frac"] - s["achieved"] / s["peak"]) < 1e-12
+    # issue slots: one warp instruction per sub-partition per clock
+    q = bench.issue_utilisation(16_777_216, 32, 0.967, 152, 2070.0)
+    assert abs(q["peak"] - 152 * 4 * 2070e6 / 1e12) < 1e-9
+    assert 0.5 < q["frac"] < 1.0 and q["inst_per_pair"] == bench.INST_PER_PAIR + 32 * bench.INST_PER_BIN
 
 
 def test_reference_arm_prints_one_json_line():
