@@ -185,6 +185,33 @@ def test_mlp_path_matches_oracle(net, bins):
     assert rel(dx[::10], truth["dx"]).max() < TOL
 
 
+@pytest.mark.parametrize("bins", [32, 64])
+def test_mlp_path_coarse_eps(net, bins):
+    """At log eps = -11 (window [-23, -11]) the network's ends, trained for e^-26, lie outside the
+    window for most pairs, so the check's Newton corrections run, and bin n is one of the bins
+    (its terms are not taken from the check above log eps = -12).  The oracle's method itself is
+    then only within its truncation error of the dense truth: the fast path must stay within three
+    times the method's largest error at the same eps plus the mixed tolerance."""
+    le = -11.0
+    v, x = W.hard_band(6000, seed=330)
+    (vf, v64), (xf, x64) = W.to_f32(v, x)
+    out = kv.kv_fwd_bwd_ex(_t(vf, torch.float32), _t(xf, torch.float32), bins=bins, bracket="mlp",
+                           mlp=net, log_eps=le, status=True)
+    lk, dv, dx = _np(out["logk"]), _np(out["dv"]), _np(out["dx"])
+    st = out["status"].cpu().numpy()
+    assert np.all(np.isfinite(lk)) and np.all(np.isfinite(dx))
+    truth = oracle.dense(v64, x64)
+    ref = oracle.o1(v64, x64, bins=bins, log_eps=le, precision="long")
+    z = v64 == 0
+    for name, got in (("logk", lk), ("dv", dv), ("dx", dx)):
+        e = rel_logk if name == "logk" else rel
+        keep = ~z if name == "dv" else np.ones(v.size, bool)
+        method = e(ref[name][keep], truth[name][keep]).max()
+        assert e(got[keep], truth[name][keep]).max() < 3 * method + TOL, (name, method)
+    assert np.all(dv[z] == 0)
+    assert np.count_nonzero(st & N.KV_PAIR_FALLBACK) < 0.05 * v.size
+
+
 def test_fallback_path_is_exact_enough():
     """A network whose outputs are NaN fails every check and sends every pair to the
     plain-bracket fallback, whose results still meet the tolerance; an untrained network is
