@@ -441,6 +441,39 @@ def extra_entries(args, kv, mlp, vf, xf, v64c, x64c, dev, stream, sms, sm_mhz, p
     return res
 
 
+def vectorised_scaling(args, kv, mlp, dev, stream):
+    """Sec. 3.4's vectorised timing: one call on arrays of N = 10 ... 10^8 pairs of the paper's
+    inputs (v = 10^{2r} - 1, x = 10^{3r - 1}), at the library's default bins.  Per N: the device
+    time of a call (CUDA events, calls back to back) and the wall time of one blocking call from
+    the host (launch + synchronize; what a user waits for on small arrays), for the learned path
+    and, up to 10^6 pairs, the FP64 path."""
+    import torch
+
+    res = {"inputs": "v = 10^(2r) - 1, x = 10^(3r - 1), r ~ U[0, 1] per element (seed 8)",
+           "learned": {}, "fp64": {}}
+    reps = max(5, args.steps)
+    for e in range(1, 9):
+        n = 10 ** e
+        v, x = W.paper_scaling(n, seed=8)
+        for path, dt, limit in (("learned", torch.float32, 10 ** 8), ("fp64", torch.float64, 10 ** 6)):
+            if n > limit:
+                continue
+            vt = torch.tensor(v, dtype=dt, device=dev)
+            xt = torch.tensor(x, dtype=dt, device=dev)
+            kw = dict(bracket="mlp", mlp=mlp) if path == "learned" else dict(bins=128)
+            out = kv.kv_fwd_bwd_ex(vt, xt, **kw)
+            total, _ = timed_steps(lambda: kv.kv_fwd_bwd_ex(vt, xt, out=out, **kw), reps, 3, stream)
+            wall = []
+            for _ in range(reps):
+                t = time.perf_counter()
+                kv.kv_fwd_bwd_ex(vt, xt, out=out, **kw)
+                torch.cuda.synchronize()
+                wall.append((time.perf_counter() - t) * 1e3)
+            res[path][str(n)] = {"device_ms": total / reps, "wall_ms": statistics.median(wall)}
+            del vt, xt, out
+    return res
+
+
 def config_entries(args, kv, mlp, dev, stream, check):
     """The other workload configurations, each timed with CUDA events and checked on a sample:
     uniform_small (4096 pairs, FP64, 128 bins, log K only), the GH log-likelihood through
@@ -725,6 +758,7 @@ def main():
         if line["fp64_plain"]:
             line["learned_vs_fp64_plain"] = value / world / line["fp64_plain"]["value"]
         line["configs"] = config_entries(args, kv, mlp, dev, stream, check)
+        line["vectorised_scaling"] = vectorised_scaling(args, kv, mlp, dev, stream)
     if world == 1 and not args.no_cpu_baseline and not f64io:
         line["cpu_baseline"] = cpu_baseline(v64c, x64c, args.bins)
     print(json.dumps(line), flush=True)
