@@ -305,6 +305,13 @@ uint64_t kv_launch_count(void);
  * default (2^22).  Process-wide; returns the previous setting (-1 for the default). */
 int kv_debug_set_wait_limit(int iterations);
 
+/* For tests of the learned fast path's bins: with on = 0 the trapezoid terms of bin n (t = t1,
+ * weight 1/2) are computed as one of the bins instead of being taken from the range check's
+ * evaluation of the right end (which the path does by default from 4 bins up and while
+ * log eps <= -12; the two agree to FP32 rounding).  Process-wide; returns the previous setting
+ * (1 = on, the default). */
+int kv_debug_set_end_terms(int on);
+
 /* Releases the device memory the library's scratch pool on the current device keeps reserved
  * (cudaMemPoolTrimTo to 0; memory of calls still in flight stays).  KV_OK if there is no pool. */
 int kv_trim_memory(void);

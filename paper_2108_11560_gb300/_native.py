@@ -31,6 +31,7 @@ KV_FLAG_PEAK_ANALYTIC_START = 1
 EXPORTED = [
     "kv_log", "kv_log_dv", "kv_log_dx", "kv_fwd_bwd", "kv_fwd_bwd_ex", "kv_fwd_bwd_host",
     "kv_fwd_bwd_host_ex", "kv_host_direct_supported", "kv_trim_memory", "kv_debug_set_wait_limit",
+    "kv_debug_set_end_terms",
     "kv_bracket", "kv_grad", "kv_grad2", "kv_sum", "kv_sum_noalloc", "kv_mlp_create", "kv_mlp_free", "kv_mlp_save",
     "kv_mlp_load", "kv_mlp_get_params", "kv_mlp_set_params", "kv_mlp_train",
     "kv_mlp_loss_grad", "kv_mlp_predict", "kv_launch_count", "kv_strerror",
@@ -74,6 +75,7 @@ def _declare(lib):
         "kv_host_direct_supported": [],
         "kv_trim_memory": [],
         "kv_debug_set_wait_limit": [I],
+        "kv_debug_set_end_terms": [I],
         "kv_bracket": [P, P, P, P, P, P, I64, I, D, I, P],
         "kv_grad": [P, P, P, P, P, I64, I, P],
         "kv_grad2": [P, P, P, P, P, P, P, P, P, P, P, I64, I, P],

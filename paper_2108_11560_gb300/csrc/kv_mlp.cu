@@ -398,6 +398,7 @@ struct MlpPathParams {
     kvh::MlpView mlp;
     MlpConst wc;
     int wait_limit;  // iterations of the per-tile wait for the tensor-core results
+    int end_terms;   // bin n's terms from the range check (see pair_tail)
 };
 
 constexpr int kMlpBlock = 128;
@@ -599,9 +600,12 @@ constexpr uint32_t kTmemCols = 64;
 // the same straight-line code into the bins.  Then FP32 bins, the finish with the float-float
 // offset, and the stores.  An edge pair's results are taken from (v, x) again after the bins, so
 // that they hold no registers during them.
-// `end`: bin n's terms from the range check (check_range), used while log eps <= kEndTermLogEps,
-// where their coarse exponent cannot matter; otherwise bin n is one of the bins.
+// `end`: bin n's terms from the range check (check_range), used while log eps <= kEndTermLogEps
+// and n >= kEndTermMinBins, where their coarse exponent cannot matter (with four or more bins one
+// of them lies within two widths of the peak, so S0 >= e^-2 while the end term is below e^le / 2);
+// otherwise bin n is one of the bins.  kv_debug_set_end_terms(0) turns them off (tests).
 constexpr float kEndTermLogEps = -12.0f;
+constexpr int kEndTermMinBins = 4;
 
 template <bool DERIV, bool D2, bool COMP = true>
 __device__ __forceinline__ void pair_tail(const MlpPathParams& p, int64_t i, bool active, bool edge, bool ok,
@@ -639,7 +643,9 @@ __device__ __forceinline__ void pair_tail(const MlpPathParams& p, int64_t i, boo
         if (edge) d2v = dvx = d2x = (isinf(x) && x > 0.0f) ? 0.0f : nanf("");
     } else {
         if (end)
-            sums_f32<1, DERIV, true, COMP>(c.b, 0, S0, S1, S2, p.log_eps <= kEndTermLogEps, end->w, end->w1, end->w2);
+            sums_f32<1, DERIV, true, COMP>(c.b, 0, S0, S1, S2,
+                                           p.end_terms && p.log_eps <= kEndTermLogEps && p.bins >= kEndTermMinBins,
+                                           end->w, end->w1, end->w2);
         else
             sums_f32<1, DERIV, true, COMP>(c.b, 0, S0, S1, S2);
     }
@@ -1308,6 +1314,7 @@ int fill_mlp_const(const kv_mlp* hc, cudaStream_t s, MlpConst* c)
 }
 
 std::atomic<int> g_wait_limit{-1};  // < 0: kWaitLimit
+std::atomic<int> g_end_terms{1};
 
 int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, uint32_t* scratch_in)
 {
@@ -1335,6 +1342,7 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
     p.log_eps = (float)log_eps;
     const int wl = g_wait_limit.load(std::memory_order_relaxed);
     p.wait_limit = wl < 0 ? kWaitLimit : wl;
+    p.end_terms = g_end_terms.load(std::memory_order_relaxed);
     rc = ensure_exp_table();
     if (rc != KV_OK) return rc;
     cudaStream_t s = (cudaStream_t)a->stream;
@@ -1623,6 +1631,11 @@ int kv_mlp_predict(const kv_mlp* h, const void* v, const void* x, void* t0, void
 int kv_debug_set_wait_limit(int iterations)
 {
     return kvh::g_wait_limit.exchange(iterations < 0 ? -1 : iterations, std::memory_order_relaxed);
+}
+
+int kv_debug_set_end_terms(int on)
+{
+    return kvh::g_end_terms.exchange(on ? 1 : 0, std::memory_order_relaxed);
 }
 
 }  // extern "C"

@@ -175,6 +175,13 @@ def debug_set_wait_limit(iterations: int) -> int:
     return int(N.lib().kv_debug_set_wait_limit(int(iterations)))
 
 
+def debug_set_end_terms(on: bool) -> int:
+    """Test hook for the fast path's bins: whether bin n's trapezoid terms come from the range
+    check's evaluation of the right end (the default) or are computed as one of the bins.
+    Returns the previous setting (1 = on)."""
+    return int(N.lib().kv_debug_set_end_terms(1 if on else 0))
+
+
 def trim_memory() -> None:
     """Release the device memory the library's scratch pool keeps reserved between calls."""
     N.check(N.lib().kv_trim_memory(), "kv_trim_memory")

@@ -212,6 +212,28 @@ def test_mlp_path_coarse_eps(net, bins):
     assert np.count_nonzero(st & N.KV_PAIR_FALLBACK) < 0.05 * v.size
 
 
+@pytest.mark.parametrize("bins", [2, 4, 5, 7, 8, 33, 44])
+def test_end_terms_from_the_check(net, bins):
+    """Bin n's trapezoid terms taken from the range check's evaluation of the right end (the
+    default, from 4 bins up) against bin n computed as one of the bins, on the same learned ranges:
+    the two agree to FP32 rounding, including bin counts that leave a scalar tail of bins and the
+    compensated instance (44 bins)."""
+    v, x = W.hard_band(20000, seed=331)
+    (vf, _), (xf, _) = W.to_f32(v, x)
+    vt, xt = _t(vf, torch.float32), _t(xf, torch.float32)
+    on = kv.kv_fwd_bwd_ex(vt, xt, bins=bins, bracket="mlp", mlp=net, status=True)
+    prev = kv.debug_set_end_terms(False)
+    try:
+        off = kv.kv_fwd_bwd_ex(vt, xt, bins=bins, bracket="mlp", mlp=net, status=True)
+    finally:
+        kv.debug_set_end_terms(True)
+    assert prev == 1
+    assert torch.equal(on["status"], off["status"])  # the same ranges
+    assert rel_logk(_np(on["logk"]), _np(off["logk"])).max() < 5e-7
+    assert rel(_np(on["dv"]), _np(off["dv"])).max() < 1e-6
+    assert rel(_np(on["dx"]), _np(off["dx"])).max() < 1e-6
+
+
 def test_fallback_path_is_exact_enough():
     """A network whose outputs are NaN fails every check and sends every pair to the
     plain-bracket fallback, whose results still meet the tolerance; an untrained network is
