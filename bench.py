@@ -101,15 +101,15 @@ ISSUE_PER_SM = 4
 # DRAM bytes per pair of the fast-path kernel (read + write) from an ncu capture of one full
 # 16,777,216-pair launch at 32 bins in steady state (the fourth of five consecutive launches, no
 # cache flush between them, so the previous launch's outputs are written back inside it):
-# 201.42 MB read + 198.86 MB written.  The algorithmic bytes per pair are v, x, grad_out in and
+# 201.53 MB read + 199.03 MB written.  The algorithmic bytes per pair are v, x, grad_out in and
 # log K, d/dv, d/dx out, 4 bytes each (402.65 MB per launch).
-TRAFFIC_BYTES_PER_PAIR = (201.41568e6 + 198.8608e6) / 16777216
+TRAFFIC_BYTES_PER_PAIR = (201.52576e6 + 199.025408e6) / 16777216
 ALGORITHMIC_BYTES_PER_PAIR = 24
 # The counts above hold for the fast-path kernel built from these sources; COUNTS_SOURCE_SHA is
 # their hash when the counts were taken.  When the sources change, the line says so and reports
 # no traffic until the counters are taken again.
 COUNTS_SOURCES = ("kv_mlp.cu", "kv_bins.cuh", "kv_dfloat.cuh")
-COUNTS_SOURCE_SHA = "6b90f7f1722eb2cd"
+COUNTS_SOURCE_SHA = "103df2a720eb558e"
 
 PATHS = {
     # name: (bracket, second derivatives, float64 I/O)
