@@ -71,7 +71,8 @@ F64_SLICE = 1 << 23     # the FP64 path's slice of the workload (134 MB of float
 #            exponent's x-part (the phi polynomials, or x cosh t from e^{+-s}, which the d/dx
 #            integrand shares) 16, the rest of the weight 2, the two derivative integrands 4
 #            (+ the tanh polynomial in the warp-blocks that need it, ~3), three sums 3 (plain
-#            block sums) or 5.25 (compensated)                             -> ~29.6 or ~32 (+ 4 MUFU)
+#            block sums) or 4.4 (compensated, one Kahan step per eight bins)
+#                                                                            -> ~29.6 or ~31 (+ 4 MUFU)
 #   per pair: layer 1 and layer 3 on the CUDA cores 256 (layer 2 runs on the tensor cores and
 #             is not counted), one peak Newton step, offset constants, endpoint check with bin
 #             n's terms, setup and finish ~190                                    -> ~446
@@ -82,8 +83,8 @@ F64_SLICE = 1 << 23     # the FP64 path's slice of the workload (134 MB of float
 PLAIN_SUMS_MAX_BINS = 40
 FP32_OPS_PER_BIN = 29.606
 FP32_OPS_PER_PAIR = 446.32
-FP32_OPS_PER_BIN_COMP = 31.886
-FP32_OPS_PER_PAIR_COMP = 445.46
+FP32_OPS_PER_BIN_COMP = 30.986
+FP32_OPS_PER_PAIR_COMP = 440.06
 MUFU_OPS_PER_BIN = 4
 # XU-pipe (MUFU) operations per pair outside the bins from the same captures
 # (smsp__inst_executed_pipe_xu x 32: 33.56 per pair and 4.0 per bin), and the XU pipe's lanes
@@ -95,21 +96,21 @@ XU_LANES_PER_SM = 32
 # much as by the FP32 pipe, so the line also reports issue-slot utilisation.
 INST_PER_BIN = 26.618
 INST_PER_PAIR = 861.3
-INST_PER_BIN_COMP = 29.642
-INST_PER_PAIR_COMP = 861.6
+INST_PER_BIN_COMP = 27.792
+INST_PER_PAIR_COMP = 851.0
 ISSUE_PER_SM = 4
 # DRAM bytes per pair of the fast-path kernel (read + write) from an ncu capture of one full
 # 16,777,216-pair launch at 32 bins in steady state (the fourth of five consecutive launches, no
 # cache flush between them, so the previous launch's outputs are written back inside it):
-# 201.53 MB read + 199.03 MB written.  The algorithmic bytes per pair are v, x, grad_out in and
+# 201.44 MB read + 198.93 MB written.  The algorithmic bytes per pair are v, x, grad_out in and
 # log K, d/dv, d/dx out, 4 bytes each (402.65 MB per launch).
-TRAFFIC_BYTES_PER_PAIR = (201.52576e6 + 199.025408e6) / 16777216
+TRAFFIC_BYTES_PER_PAIR = (201.437696e6 + 198.926848e6) / 16777216
 ALGORITHMIC_BYTES_PER_PAIR = 24
 # The counts above hold for the fast-path kernel built from these sources; COUNTS_SOURCE_SHA is
 # their hash when the counts were taken.  When the sources change, the line says so and reports
 # no traffic until the counters are taken again.
 COUNTS_SOURCES = ("kv_mlp.cu", "kv_bins.cuh", "kv_dfloat.cuh")
-COUNTS_SOURCE_SHA = "103df2a720eb558e"
+COUNTS_SOURCE_SHA = "2e70807a0a47b452"
 
 PATHS = {
     # name: (bracket, second derivatives, float64 I/O)
