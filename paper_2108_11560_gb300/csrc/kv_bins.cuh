@@ -715,12 +715,17 @@ __device__ __forceinline__ float2 expm1_small2(float2 y)
 // (Kahan) across blocks.
 constexpr int kBlockSums2 = 8;
 
-// Two bins (the components of s; c = their weight factors c_m e^{-lu}) of the seven sums, in
-// paired FP32 instructions, added to acc: the fast path's weight split w = c (1 + e^{-2vt})
-// 2^{c1 s + N(s)} (no log1p), 1/(1 + e^{-2vt}) from the approximate reciprocal, tanh(vt) from its
-// polynomial below vt = 0.35, e^{-2vt} - e^{-2u} as e^{-2u} expm1(-2vs) from a polynomial where
-// |2vs| < 1/2, and dc = cosh t - cosh t_p = sinh t_p s + (e^{t_p} phi(s) + e^{-t_p} phi(-s))/2.
-__device__ __forceinline__ void sums2_bins2(const BinsF& b, const BinsK& kk, float2 s, float2 c,
+// Two bins (the components of s) of the seven sums, in paired FP32 instructions, added to acc:
+// the fast path's weight split w = (1 + e^{-2vt}) 2^{c1 s + N(s) + cl} without the per-pair factor
+// e^{-lu} (every sum carries it, so the moments do not see it; sums2_f32 applies it to S0), cl the
+// trapezoid factor's log2 (-1 at the end bins, else 0); 1/(1 + e^{-2vt}) from the approximate
+// reciprocal, tanh(vt) from its polynomial below vt = 0.35, e^{-2vt} - e^{-2u} as
+// e^{-2u} expm1(-2vs) from a polynomial where |2vs| < 1/2, and
+// dc = cosh t - cosh t_p = sinh t_p s + (e^{t_p} phi(s) + e^{-t_p} phi(-s))/2; acc[6] is the sum
+// of w t^2 sech^2(vt) / 4.  With VOTE (all 32 lanes of the warp in the call) the two polynomials
+// are evaluated only when some lane of the warp needs them.
+template <bool VOTE>
+__device__ __forceinline__ void sums2_bins2(const BinsF& b, const BinsK& kk, float2 s, float2 cl,
                                             float (&acc)[7])
 {
     const float2 z = mul2(s, s);
@@ -739,19 +744,31 @@ __device__ __forceinline__ void sums2_bins2(const BinsF& b, const BinsK& kk, flo
     const float2 e2 = make_float2(ex2_approx(ea.x), ex2_approx(ea.y));  // e^{-2vt}
     const float2 ope = add2(f2(1.0f), e2);
     const float2 rope = make_float2(rcp_approx(ope.x), rcp_approx(ope.y));
-    const float2 dg = fma2(f2(kk.c1), s, fma2(f2(kk.nap), php, mul2(f2(kk.nam), phm)));
-    const float2 w = mul2(mul2(c, ope), make_float2(ex2_approx(dg.x), ex2_approx(dg.y)));
+    const float2 dg = fma2(f2(kk.c1), s, fma2(f2(kk.nap), php, fma2(f2(kk.nam), phm, cl)));
+    const float2 w = mul2(ope, make_float2(ex2_approx(dg.x), ex2_approx(dg.y)));
     const float2 vt = fma2(f2(b.v), s, f2(b.u));
-    const float2 ts = tanh_small2(vt), tl = mul2(sub2(f2(1.0f), e2), rope);
-    const float2 th = make_float2(vt.x < TANH_SERIES_MAX ? ts.x : tl.x, vt.y < TANH_SERIES_MAX ? ts.y : tl.y);
+    float2 th = mul2(sub2(f2(1.0f), e2), rope);
+    {
+        const bool kx = vt.x < TANH_SERIES_MAX, ky = vt.y < TANH_SERIES_MAX;
+        if (!VOTE || __any_sync(0xffffffffu, kx || ky)) {
+            const float2 ts = tanh_small2(vt);
+            th = make_float2(kx ? ts.x : th.x, ky ? ts.y : th.y);
+        }
+    }
     const float2 t = add2(f2(b.tp), s);
     const float2 vs2 = mul2(f2(-2.0f * b.v), s);
-    const float2 des = mul2(f2(b.e2u), expm1_small2(vs2)), del = sub2(e2, f2(b.e2u));
-    const float2 de = make_float2(fabsf(vs2.x) < 0.5f ? des.x : del.x, fabsf(vs2.y) < 0.5f ? des.y : del.y);
+    float2 de = sub2(e2, f2(b.e2u));
+    {
+        const bool kx = fabsf(vs2.x) < 0.5f, ky = fabsf(vs2.y) < 0.5f;
+        if (!VOTE || __any_sync(0xffffffffu, kx || ky)) {
+            const float2 des = mul2(f2(b.e2u), expm1_small2(vs2));
+            de = make_float2(kx ? des.x : de.x, ky ? des.y : de.y);
+        }
+    }
     const float2 da = fma2(s, th, mul2(f2(-2.0f * b.tp * kk.kc), mul2(de, rope)));
-    const float2 dc = fma2(f2(b.shp), s, mul2(f2(0.5f), fma2(f2(b.ep), php, mul2(f2(b.em), phm))));
+    const float2 dc = fma2(f2(b.shp), s, fma2(f2(kk.hep), php, mul2(f2(kk.hem), phm)));
     const float2 wda = mul2(w, da), wdc = mul2(w, dc);
-    const float2 wq = mul2(mul2(w, mul2(t, t)), mul2(f2(4.0f), mul2(e2, mul2(rope, rope))));  // w t^2 sech^2(vt)
+    const float2 wq = mul2(mul2(w, mul2(t, t)), mul2(e2, mul2(rope, rope)));  // w t^2 sech^2(vt) / 4
     acc[0] += w.x + w.y;
     acc[1] += wda.x + wda.y;
     acc[2] = fmaf(wda.x, da.x, fmaf(wda.y, da.y, acc[2]));
@@ -761,9 +778,7 @@ __device__ __forceinline__ void sums2_bins2(const BinsF& b, const BinsK& kk, flo
     acc[6] += wq.x + wq.y;
 }
 
-// The seven sums over bins m = lane, lane + L, ... <= n, two bins per instruction (a last odd
-// bin runs as a pair whose second weight is 0).
-template <int L>
+template <int L, bool VOTE = false>
 __device__ Sums2<float> sums2_f32(const BinsF& b, int lane)
 {
     const BinsK kk = bins_k(b);
@@ -778,8 +793,8 @@ __device__ Sums2<float> sums2_f32(const BinsF& b, int lane)
     float mf = (float)lane;
     for (; m + L <= b.n; m += 2 * L, mf += (float)(2 * L)) {
         const float2 s = fma2(make_float2(mf, mf + (float)L), f2(b.h), f2(b.s0));
-        const float2 c = make_float2(m == 0 ? 0.5f * kk.kc : kk.kc, m + L == b.n ? 0.5f * kk.kc : kk.kc);
-        sums2_bins2(b, kk, s, c, acc);
+        const float2 cl = make_float2(m == 0 ? -1.0f : 0.0f, m + L == b.n ? -1.0f : 0.0f);
+        sums2_bins2<VOTE>(b, kk, s, cl, acc);
         in_block += 2;
         if (in_block == kBlockSums2) {
             for (int j = 0; j < 7; ++j) {
@@ -790,11 +805,21 @@ __device__ Sums2<float> sums2_f32(const BinsF& b, int lane)
         }
     }
     if (m <= b.n) {
+        // the one bin left (the second component's weight is zeroed through its exponent)
         const float s = fmaf(mf, b.h, b.s0);
-        sums2_bins2(b, kk, f2(s), make_float2((m == 0 || m == b.n) ? 0.5f * kk.kc : kk.kc, 0.0f), acc);
+        sums2_bins2<VOTE>(b, kk, f2(s), make_float2((m == 0 || m == b.n) ? -1.0f : 0.0f, -INFINITY), acc);
     }
     for (int j = 0; j < 7; ++j) k[j].add(acc[j]);
-    return lane_sums2<float, L>(k);
+    // the factor e^{-lu} the bins left out, and sech^2(vt) = 4 e^{-2vt} / (1 + e^{-2vt})^2
+    Sums2<float> r = lane_sums2<float, L>(k);
+    r.s0 *= kk.kc;
+    r.a1 *= kk.kc;
+    r.a2 *= kk.kc;
+    r.c1 *= kk.kc;
+    r.c2 *= kk.kc;
+    r.x *= kk.kc;
+    r.q *= 4.0f * kk.kc;
+    return r;
 }
 
 }  // namespace kvd

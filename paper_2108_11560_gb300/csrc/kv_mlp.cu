@@ -630,7 +630,7 @@ __device__ __forceinline__ void pair_tail(const MlpPathParams& p, int64_t i, boo
     float d2v = 0.0f, dvx = 0.0f, d2x = 0.0f;
     if constexpr (D2) {
         // second derivatives (and the first ones) from the shifted sums
-        const Sums2<float> m = sums2_f32<1>(c.b, 0);
+        const Sums2<float> m = sums2_f32<1, true>(c.b, 0);
         S0 = m.s0;
         const float ar = tr * (c.b.u < TANH_SERIES_MAX ? tanh_small(c.b.u)
                                                         : (1.0f - c.b.e2u) / (1.0f + c.b.e2u));
