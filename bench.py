@@ -102,15 +102,15 @@ ISSUE_PER_SM = 4
 # DRAM bytes per pair of the fast-path kernel (read + write) from an ncu capture of one full
 # 16,777,216-pair launch at 32 bins in steady state (the fourth of five consecutive launches, no
 # cache flush between them, so the previous launch's outputs are written back inside it):
-# 201.44 MB read + 198.93 MB written.  The algorithmic bytes per pair are v, x, grad_out in and
+# 201.44 MB read + 198.81 MB written.  The algorithmic bytes per pair are v, x, grad_out in and
 # log K, d/dv, d/dx out, 4 bytes each (402.65 MB per launch).
-TRAFFIC_BYTES_PER_PAIR = (201.437696e6 + 198.926848e6) / 16777216
+TRAFFIC_BYTES_PER_PAIR = (201.43744e6 + 198.806016e6) / 16777216
 ALGORITHMIC_BYTES_PER_PAIR = 24
 # The counts above hold for the fast-path kernel built from these sources; COUNTS_SOURCE_SHA is
 # their hash when the counts were taken.  When the sources change, the line says so and reports
 # no traffic until the counters are taken again.
 COUNTS_SOURCES = ("kv_mlp.cu", "kv_bins.cuh", "kv_dfloat.cuh")
-COUNTS_SOURCE_SHA = "2e70807a0a47b452"
+COUNTS_SOURCE_SHA = "f09091775a7beea4"
 
 PATHS = {
     # name: (bracket, second derivatives, float64 I/O)
