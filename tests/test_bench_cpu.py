@@ -114,3 +114,23 @@ def test_plain_sums_threshold_matches_the_kernels():
     with open(os.path.join(ROOT, "paper_2108_11560_gb300", "csrc", "kv_bins.cuh")) as f:
         m = re.search(r"constexpr int kPlainSumsMaxBins = (\d+);", f.read())
     assert m and int(m.group(1)) == bench.PLAIN_SUMS_MAX_BINS
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """Launched as the multi-GPU contract launches it (torchrun, two ranks): rank 0 alone runs the
+    oracle arm and prints its one line, the other rank exits 0 without work."""
+    import socket
+
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port),
+                        os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=900, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
