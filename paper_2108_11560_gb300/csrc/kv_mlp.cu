@@ -727,14 +727,17 @@ __global__ void __launch_bounds__(kMlpBlock, D2 ? 6 : 8) kv_mlp_tc_kernel(MlpPat
     __shared__ __align__(1024) TcSmem sm;
     const int t = threadIdx.x;
     const int warp = t >> 5;
-    for (int k = t; k < H * H; k += kMlpBlock)
-        *reinterpret_cast<unsigned short*>(sm.b + tile_off(k / H, k % H)) = p.mlp.w2h[k];
-    for (int k = t; k < H * 16; k += kMlpBlock) {  // b2 = hi + lo in BF16 at k = 0, 1
-        const int n = k >> 4, kk = k & 15;
-        const float b2 = p.mlp.b2[n];
+    // W2 into its K-major tile, eight BF16 (one 16-byte core-matrix row) per load and store
+    for (int q = t; q < H * H / 8; q += kMlpBlock) {
+        const int k = 8 * q;
+        *reinterpret_cast<uint4*>(sm.b + tile_off(k / H, k % H)) = __ldg(reinterpret_cast<const uint4*>(p.mlp.w2h) + q);
+    }
+    if (t < H) {  // row t of the bias slice: b2 = hi + lo in BF16 at k = 0, 1, zeros elsewhere
+        const float b2 = p.mlp.b2[t];
         const unsigned short hi = bf16_bits(b2);
-        const unsigned short val = kk == 0 ? hi : kk == 1 ? bf16_bits(b2 - bf16_value(hi)) : 0;
-        *reinterpret_cast<unsigned short*>(sm.bb + slice_off(n, kk)) = val;
+        const unsigned short lo = bf16_bits(b2 - bf16_value(hi));
+        *reinterpret_cast<uint4*>(sm.bb + slice_off(t, 0)) = make_uint4((uint32_t)hi | ((uint32_t)lo << 16), 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(sm.bb + slice_off(t, 8)) = make_uint4(0u, 0u, 0u, 0u);
     }
     if (t < 8 * 16)
         *reinterpret_cast<unsigned short*>(sm.ones + slice_off(t >> 4, t & 15)) = (t & 15) < 2 ? 0x3F80 : 0;
