@@ -87,30 +87,30 @@ FP32_OPS_PER_BIN_COMP = 30.986
 FP32_OPS_PER_PAIR_COMP = 440.06
 MUFU_OPS_PER_BIN = 4
 # XU-pipe (MUFU) operations per pair outside the bins from the same captures
-# (smsp__inst_executed_pipe_xu x 32: 33.56 per pair and 4.0 per bin), and the XU pipe's lanes
+# (smsp__inst_executed_pipe_xu x 32: 33.34 per pair and 4.0 per bin), and the XU pipe's lanes
 # per SM per clock that ncu's XU percentages are taken against.
-MUFU_OPS_PER_PAIR = 33.56
+MUFU_OPS_PER_PAIR = 33.34
 XU_LANES_PER_SM = 32
 # Warp instructions issued per pair (smsp__inst_executed x 32 / pairs, same captures): the fast
 # path is bound by instruction issue (one warp instruction per SM sub-partition per clock) as
 # much as by the FP32 pipe, so the line also reports issue-slot utilisation.
 INST_PER_BIN = 26.618
-INST_PER_PAIR = 861.3
+INST_PER_PAIR = 844.6
 INST_PER_BIN_COMP = 27.792
-INST_PER_PAIR_COMP = 851.0
+INST_PER_PAIR_COMP = 834.3
 ISSUE_PER_SM = 4
 # DRAM bytes per pair of the fast-path kernel (read + write) from an ncu capture of one full
 # 16,777,216-pair launch at 32 bins in steady state (the fourth of five consecutive launches, no
 # cache flush between them, so the previous launch's outputs are written back inside it):
-# 201.44 MB read + 198.81 MB written.  The algorithmic bytes per pair are v, x, grad_out in and
+# 201.38 MB read + 199.01 MB written.  The algorithmic bytes per pair are v, x, grad_out in and
 # log K, d/dv, d/dx out, 4 bytes each (402.65 MB per launch).
-TRAFFIC_BYTES_PER_PAIR = (201.43744e6 + 198.806016e6) / 16777216
+TRAFFIC_BYTES_PER_PAIR = (201.376256e6 + 199.007744e6) / 16777216
 ALGORITHMIC_BYTES_PER_PAIR = 24
 # The counts above hold for the fast-path kernel built from these sources; COUNTS_SOURCE_SHA is
 # their hash when the counts were taken.  When the sources change, the line says so and reports
 # no traffic until the counters are taken again.
 COUNTS_SOURCES = ("kv_mlp.cu", "kv_bins.cuh", "kv_dfloat.cuh")
-COUNTS_SOURCE_SHA = "f09091775a7beea4"
+COUNTS_SOURCE_SHA = "14b10da725e62105"
 
 PATHS = {
     # name: (bracket, second derivatives, float64 I/O)

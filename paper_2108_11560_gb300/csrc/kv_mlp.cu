@@ -1393,7 +1393,10 @@ int launch_mlp_path(const kv_args* a, int bins, double log_eps, int max_iter, ui
         f.flags = a->flags;
         f.try_f32 = f32_plain ? 0 : 1;
         f.fallback_total = a->fallback_count;
-        int grid = sm_count();  // grid-stride over the list; most calls have none
+        // grid-stride over the list (most calls have none), no more CTAs than the list can fill
+        const int64_t most = (a->n + kMlpBlock - 1) / kMlpBlock;
+        int grid = sm_count();
+        if (most < grid) grid = (int)most;
         if (second) kv_fallback_kernel<true, true><<<grid, kMlpBlock, 0, s>>>(f);
         else if (deriv) kv_fallback_kernel<true><<<grid, kMlpBlock, 0, s>>>(f);
         else kv_fallback_kernel<false><<<grid, kMlpBlock, 0, s>>>(f);
